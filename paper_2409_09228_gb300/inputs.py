@@ -1,0 +1,187 @@
+"""Seeded synthetic inputs for the track fit: tracks, hits, detector surfaces.
+
+This module draws the workload only.  It holds none of the fit's arithmetic
+(no propagation of a fitted state, no Jacobian, covariance transport or Kalman
+update): the truth trajectories are helices through the origin, whose surface
+crossings have the simple closed forms below, and the hits are those crossings
+smeared by Gaussian noise.  Both the GPU library's tests and the CPU oracle
+take their inputs from here.
+
+Workload (paper Sec. 3.1): one seed track smeared per track, one hit per layer
+smeared per track.  Distributions are the synthetic stand-ins this library is
+measured on:
+  * p2r: cylinders at radii uniformly spaced 4..110 cm; |eta| < 1.
+  * p2z: planes at z uniformly spaced 10..270 cm; eta in [1.5, 2.5].
+  * pT ~ U[0.5, 10] GeV, phi ~ U[0, 2 pi), q = +-1 with probability 1/2,
+    theta = 2 atan(exp(-eta)); B = 3.8 T along +z.
+  * p2r only: a track whose transverse circle has diameter 2 rho reaches
+    radius R only if R <= 2 rho, and crosses it tangentially at R = 2 rho.
+    pT is drawn from U[0.5, 10] conditioned on R_max / (2 rho) <= 0.9, i.e.
+    U[pT_min, 10] with pT_min = kA B R_max / 1.8 (0.697 GeV at 110 cm, 3.8 T).
+  * hits: p2r moves the crossing along the cylinder by N(0, 0.01 cm) in r-phi
+    and N(0, 0.1 cm) in z; p2z moves it in the plane by N(0, 0.01 cm) along
+    the azimuthal direction and N(0, 0.1 cm) along the radial direction.  The
+    hit covariance is the matching rank-2 3x3 matrix.
+  * initial state: the truth at the vertex plus N(0, sigma0) with
+    sigma0 = (0.01, 0.01, 0.1 cm, 0.05 w, 0.01 rad, 0.01 rad); covariance
+    diag(sigma0^2).
+
+Random numbers come from numpy's Philox counter-based generator, one
+independent stream per (seed, quantity), drawn in track order, so the inputs
+do not depend on thread counts or on how the work is later split.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+KA = 0.00299792458  # GeV / (T cm)
+B_FIELD = 3.8
+NLAYER = 20
+MODE_R = 0
+MODE_Z = 1
+SIGMA0 = (0.01, 0.01, 0.1, 0.05, 0.01, 0.01)  # w entry is relative
+SIGMA_RPHI = 0.01
+SIGMA_2 = 0.1  # z for p2r, radial for p2z
+
+_STREAM_PT, _STREAM_ETA, _STREAM_PHI, _STREAM_Q, _STREAM_INIT, _STREAM_HIT = range(6)
+
+
+def surfaces(mode: int, nlayer: int = NLAYER) -> np.ndarray:
+    """Layer positions: radii 4..110 cm (p2r) or z 10..270 cm (p2z), float32."""
+    if mode == MODE_R:
+        return np.linspace(4.0, 110.0, nlayer).astype(np.float32)
+    return np.linspace(10.0, 270.0, nlayer).astype(np.float32)
+
+
+def pt_min_p2r(B: float, rmax: float, frac: float = 0.9) -> float:
+    return KA * B * rmax / (2.0 * frac)
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=(int(seed) << 8) | stream))
+
+
+@dataclass
+class TrackSet:
+    mode: int
+    B: float
+    surf: np.ndarray          # (nlayer,) float32
+    par0: np.ndarray          # (6, n) float32: x, y, z, w=1/pT, phi, theta
+    cov0: np.ndarray          # (21, n) float32, packed lower triangle
+    q: np.ndarray             # (n,) int32
+    hpos: np.ndarray          # (nlayer, 3, n) float32
+    hcov: np.ndarray          # (nlayer, 6, n) float32, (xx, yx, yy, zx, zy, zz)
+    truth: Optional[np.ndarray] = field(default=None)  # (nlayer, 6, n) float64
+
+    @property
+    def n(self) -> int:
+        return self.par0.shape[1]
+
+    @property
+    def nlayer(self) -> int:
+        return self.hpos.shape[0]
+
+    def subset(self, idx) -> "TrackSet":
+        idx = np.asarray(idx)
+        return TrackSet(self.mode, self.B, self.surf, np.ascontiguousarray(self.par0[:, idx]),
+                        np.ascontiguousarray(self.cov0[:, idx]), np.ascontiguousarray(self.q[idx]),
+                        np.ascontiguousarray(self.hpos[:, :, idx]),
+                        np.ascontiguousarray(self.hcov[:, :, idx]),
+                        None if self.truth is None else np.ascontiguousarray(self.truth[:, :, idx]))
+
+
+def generate(mode: int, n: int, seed: int, nlayer: int = NLAYER, B: float = B_FIELD,
+             surf: Optional[np.ndarray] = None, pt_range=(0.5, 10.0), eta_range=None,
+             want_truth: bool = False, sigma_rphi: float = SIGMA_RPHI,
+             sigma_2: float = SIGMA_2) -> TrackSet:
+    """n independent tracks of one mode with hits on nlayer surfaces."""
+    surf = surfaces(mode, nlayer) if surf is None else np.asarray(surf, np.float32)
+    nlayer = surf.shape[0]
+    s64 = surf.astype(np.float64)
+    B = float(np.float32(B))
+    lo, hi = pt_range
+    if mode == MODE_R:
+        lo = max(lo, pt_min_p2r(B, float(s64.max())))
+        eta_lo, eta_hi = (-1.0, 1.0) if eta_range is None else eta_range
+    else:
+        eta_lo, eta_hi = (1.5, 2.5) if eta_range is None else eta_range
+    pt = _rng(seed, _STREAM_PT).uniform(lo, hi, n)
+    eta = _rng(seed, _STREAM_ETA).uniform(eta_lo, eta_hi, n)
+    phi0 = _rng(seed, _STREAM_PHI).uniform(0.0, 2.0 * np.pi, n)
+    q = np.where(_rng(seed, _STREAM_Q).random(n) < 0.5, -1, 1).astype(np.int32)
+    theta = 2.0 * np.arctan(np.exp(-eta))
+    w = 1.0 / pt
+    cot = 1.0 / np.tan(theta)
+    rho = pt / (KA * B)  # transverse radius of curvature [cm]
+
+    noise = _rng(seed, _STREAM_HIT)
+    hpos = np.empty((nlayer, 3, n), np.float32)
+    hcov = np.zeros((nlayer, 6, n), np.float32)
+    truth = np.empty((nlayer, 6, n)) if want_truth else None
+    for l in range(nlayer):
+        s = s64[l]
+        n1 = noise.standard_normal(n)
+        n2 = noise.standard_normal(n)
+        if mode == MODE_R:
+            # A circle through the origin reaches radius R after turning by
+            # 2 asin(R / 2 rho); the crossing sits on the chord direction.
+            half = np.arcsin(s / (2.0 * rho))
+            h = 2.0 * rho * half
+            chord_phi = phi0 - q * half
+            z = h * cot
+            phi_hit = chord_phi + n1 * sigma_rphi / s
+            c, sn = np.cos(phi_hit), np.sin(phi_hit)
+            hpos[l, 0], hpos[l, 1], hpos[l, 2] = s * c, s * sn, z + n2 * sigma_2
+            vr = sigma_rphi ** 2
+            hcov[l, 0] = vr * sn * sn
+            hcov[l, 1] = -vr * sn * c
+            hcov[l, 2] = vr * c * c
+            hcov[l, 5] = sigma_2 ** 2
+            if want_truth:
+                truth[l] = (s * np.cos(chord_phi), s * np.sin(chord_phi), z, w,
+                            phi0 - 2.0 * q * half, theta)
+        else:
+            # Transverse path to the plane, then the chord of that arc.
+            h = s * np.tan(theta)
+            half = -q * h / (2.0 * rho)
+            chord = h * np.sinc(half / np.pi)  # numpy: sinc(x) = sin(pi x)/(pi x)
+            x = chord * np.cos(phi0 + half)
+            y = chord * np.sin(phi0 + half)
+            r = np.hypot(x, y)
+            ux, uy = x / r, y / r          # radial direction in the plane
+            tx, ty = -uy, ux               # azimuthal direction in the plane
+            hpos[l, 0] = x + n1 * sigma_rphi * tx + n2 * sigma_2 * ux
+            hpos[l, 1] = y + n1 * sigma_rphi * ty + n2 * sigma_2 * uy
+            hpos[l, 2] = s
+            a, b = sigma_rphi ** 2, sigma_2 ** 2
+            hcov[l, 0] = a * tx * tx + b * ux * ux
+            hcov[l, 1] = a * ty * tx + b * uy * ux
+            hcov[l, 2] = a * ty * ty + b * uy * uy
+            if want_truth:
+                truth[l] = (x, y, np.full(n, s), w, phi0 + 2.0 * half, theta)
+
+    init = _rng(seed, _STREAM_INIT).standard_normal((6, n))
+    sig = np.stack([np.full(n, SIGMA0[0]), np.full(n, SIGMA0[1]), np.full(n, SIGMA0[2]),
+                    SIGMA0[3] * w, np.full(n, SIGMA0[4]), np.full(n, SIGMA0[5])])
+    truth0 = np.stack([np.zeros(n), np.zeros(n), np.zeros(n), w, phi0, theta])
+    par0 = (truth0 + sig * init).astype(np.float32)
+    cov0 = np.zeros((21, n), np.float32)
+    for i in range(6):
+        cov0[i * (i + 1) // 2 + i] = (sig[i] ** 2).astype(np.float32)
+    return TrackSet(mode, B, surf, par0, cov0, q, hpos, hcov, truth)
+
+
+def uneven_event_sizes(nevt: int, seed: int, median: float = 2000.0, sigma_ln: float = 1.0,
+                       lo: int = 50, hi: int = 20000) -> np.ndarray:
+    """Track counts per event: log-normal (median, sigma_ln) clipped to [lo, hi]."""
+    g = _rng(seed, 16)
+    ntrk = np.exp(np.log(median) + sigma_ln * g.standard_normal(nevt))
+    return np.clip(np.rint(ntrk), lo, hi).astype(np.int64)
+
+
+def uneven_event_modes(nevt: int, seed: int) -> np.ndarray:
+    """Mode per event, p2r or p2z with probability 1/2."""
+    return np.where(_rng(seed, 17).random(nevt) < 0.5, MODE_R, MODE_Z).astype(np.int32)
