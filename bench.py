@@ -1,0 +1,370 @@
+"""Benchmark of the fused propagate + Kalman-update kernels on GB300.
+
+One step = the whole hot path over one batch: p2r on 100 events x 9600 tracks
+x 20 cylinders (one launch) and p2z on 100 x 9600 x 20 planes (one launch).
+Metric: track-layer propagate+update per second (kernel time, inputs resident
+in HBM).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 runs under torchrun, one rank per GPU; every rank fits its own batch of
+the same size (weak scaling, no data exchange) and rank 0 reports the
+whole-job throughput over the slowest rank's time.  --impl reference times the
+FP64 CPU oracle on the host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NEVT, NTRK, NLAYER, SEED = 100, 9600, 20, 2
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+# Algorithmic work per track-layer (FP32 flops of the formulas, FMA = 2, as
+# counted in the design doc) and bytes (hit 36 B + track in/out 229 B / nlayer).
+FLOPS_P2Z = 570.0
+FLOPS_P2R_BASE = 703.0
+FLOPS_P2R_PER_ITER = 66.0
+BYTES_TRACK_IN = (6 + 21 + 1) * 4
+BYTES_TRACK_OUT = (6 + 21 + 1 + 1) * 4 + 1
+
+
+def set_nevt(n: int) -> None:
+    global NEVT
+    NEVT = n
+
+
+def bytes_per_track_layer(nlayer: int) -> float:
+    return 36.0 + (BYTES_TRACK_IN + BYTES_TRACK_OUT) / nlayer
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured",
+                "sm_max_mhz": float(d.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL))}
+    return {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": SM_MAX_MHZ_NOMINAL}
+
+
+def fp32_peak_tflops(mhz: float) -> float:
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_09228_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{NEVT}x{NTRK}x{NLAYER}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    m_val = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_val or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_val.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def dist_setup(gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(rank: int):
+    from paper_2409_09228_gb300 import inputs
+    n = NEVT * NTRK
+    sets = [inputs.generate(m, n, seed=SEED + 1000 * rank, nlayer=NLAYER) for m in (0, 1)]
+    return sets
+
+
+def cpu_baseline(sets, budget_s: float = 12.0) -> dict:
+    """The FP64 oracle on the host cores over whole events, until budget_s elapses."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    done, t0 = 0, time.perf_counter()
+    evts = 0
+    while evts < NEVT and time.perf_counter() - t0 < budget_s:
+        for ts in sets:
+            sub = ts.subset(np.arange(evts * NTRK, (evts + 1) * NTRK))
+            oracle.fit_set(sub, nthreads=cores)
+            done += NTRK * NLAYER
+        evts += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "track-layer/s", "cores": cores, "kind": "oracle",
+            "sample": f"{evts} of {NEVT} events of each mode (p2r + p2z, {NTRK} tracks x "
+                      f"{NLAYER} layers each), FP64, {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2409_09228_gb300 import inputs
+    cores = len(os.sched_getaffinity(0))
+    ev_per_step = 1
+    sets = [inputs.generate(m, ev_per_step * NTRK, seed=SEED, nlayer=NLAYER) for m in (0, 1)]
+    for _ in range(args.warmup):
+        for ts in sets:
+            oracle.fit_set(ts, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for ts in sets:
+            oracle.fit_set(ts, nthreads=cores)
+    dt = (time.perf_counter() - t0) / args.steps
+    units = 2 * ev_per_step * NTRK * NLAYER
+    v = units / dt
+    line = {"impl": "reference", "metric": "track-layer propagate+update/s",
+            "value": v, "unit": "track-layer/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v, "unit": "track-layer/s",
+                             "sample": f"{ev_per_step} event of each mode per step "
+                                       f"({units} track-layers)"},
+            "e2e": {"value": v, "unit": "track-layer/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def config_dict(args):
+    return {"workload": f"p2r + p2z fused fit, {NEVT} events x {NTRK} tracks x {NLAYER} layers "
+                        f"per mode, one launch per mode",
+            "nevt": NEVT, "ntrk": NTRK, "nlayer": NLAYER, "modes": ["p2r", "p2z"],
+            "global_batch": args.gpus * 2 * NEVT * NTRK, "parallelism": f"dp{args.gpus}",
+            "l2": "inputs larger than L2 (691 MB of hits per mode per step); no flush"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--nevt", type=int, default=NEVT, help="events per mode (default 100)")
+    args = ap.parse_args()
+    set_nevt(args.nevt)
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_2409_09228_gb300 import fit
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    fit.load()
+    sets = workload(rank)
+    geoms = [fit.Geometry(s.B, s.surf) for s in sets]
+    f = fit.Fitter(geoms[0], geoms[1], device=local)
+    n = NEVT * NTRK
+    ld = n
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    dev_in = [[up(a) for a in (s.par0, s.cov0, s.q, s.hpos, s.hcov)] for s in sets]
+    outs = [f.outputs(n, ld=ld) for _ in sets]
+    ntrk = [NTRK] * NEVT
+    stream = torch.cuda.current_stream(dev)
+
+    def step(events=None):
+        for m in (0, 1):
+            if events is not None:
+                events[m][0].record(stream)
+            f.run(*dev_in[m], ntrk, [m] * NEVT, out=outs[m], stream=stream)
+            if events is not None:
+                events[m][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    st = f.sync(stream)
+    assert st["nonfinite"] == 0 and st["no_intersection"] == 0, st
+    per = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(2)]
+           for _ in range(args.steps)]
+    t_begin, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    t_begin.record(stream)
+    for k in range(args.steps):
+        step(per[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier(world)
+    ms = t_begin.elapsed_time(t_end) / args.steps
+    ms = max_over_ranks(world, ms)
+    kernel_ms = [statistics.mean(per[k][m][0].elapsed_time(per[k][m][1]) for k in range(args.steps))
+                 for m in (0, 1)]
+    st = f.sync(stream)
+    units_per_step = 2 * n * NLAYER
+    value = world * units_per_step / (ms / 1e3)
+
+    # iterations of the p2r path-length step, for the algorithmic flop count
+    it_per = st.get("iterations", 0) / max(1, args.steps * n * NLAYER) if "iterations" in st else None
+    flops = [FLOPS_P2R_BASE + FLOPS_P2R_PER_ITER * (it_per if it_per else 3.0), FLOPS_P2Z]
+    dom = int(np.argmax(kernel_ms))
+    name = ["fit_fused_p2r", "fit_fused_p2z"][dom]
+    peaks = load_peaks()
+    alu_peak = fp32_peak_tflops(peaks["sm_max_mhz"])
+    tl = n * NLAYER
+    alu_ach = flops[dom] * tl / (kernel_ms[dom] / 1e3) / 1e12
+    hbm_ach = bytes_per_track_layer(NLAYER) * tl / (kernel_ms[dom] / 1e3) / 1e9
+    t_alu = flops[dom] * tl / (alu_peak * 1e12)
+    t_hbm = bytes_per_track_layer(NLAYER) * tl / (peaks["hbm_gbs"] * 1e9)
+    traffic = profiled_traffic(name)
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": alu_ach / alu_peak,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_ach / peaks["hbm_gbs"], "peak_source": peaks["source"]}
+    roof.update({"traffic": traffic, "kernel": name, "kernel_ms": kernel_ms[dom],
+                 "flops_per_track_layer": flops[dom],
+                 "bytes_per_track_layer": bytes_per_track_layer(NLAYER),
+                 "hbm_frac": hbm_ach / peaks["hbm_gbs"], "alu_frac": alu_ach / alu_peak,
+                 "kernel_ms_p2r_p2z": kernel_ms})
+
+    # End to end: pinned host buffers -> device -> fused fit -> host, per step.
+    pinned_in = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                  for a in (s.par0, s.cov0, s.q, s.hpos, s.hcov)] for s in sets]
+    pinned_out = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
+                   for k, v in o.items() if v is not None} for o in outs]
+    h2d = sum(t.numel() * t.element_size() for p in pinned_in for t in p)
+    d2h = sum(t.numel() * t.element_size() for p in pinned_out for t in p.values())
+
+    def e2e_step():
+        for m in (0, 1):
+            for d, h in zip(dev_in[m], pinned_in[m]):
+                d.copy_(h, non_blocking=True)
+            f.run(*dev_in[m], ntrk, [m] * NEVT, out=outs[m], stream=stream)
+            for k, h in pinned_out[m].items():
+                h.copy_(outs[m][k], non_blocking=True)
+
+    e2e_ms = float("nan")
+    if args.e2e_steps > 0:
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = max_over_ranks(world, e0.elapsed_time(e1) / args.e2e_steps)
+    f.sync(stream)
+    f.close()
+
+    if rank != 0:
+        return
+    line = {"metric": "track-layer propagate+update/s", "value": value, "unit": "track-layer/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator, paper Sec. 3.1 smearing)",
+            "config": config_dict(args), "roofline": roof, "clocks": clk,
+            "e2e": {"value": world * units_per_step / (e2e_ms / 1e3), "unit": "track-layer/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "path": "pinned host -> HBM copies, fit_propagate_update, HBM -> pinned host"},
+            "gpu_launches": 2 * args.steps, "p2r_iterations_per_track_layer": it_per}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sets)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

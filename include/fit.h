@@ -1,0 +1,156 @@
+/*
+ * fit.h -- C ABI of libfit, the GB300 (sm_103a) fused track propagation +
+ * Kalman update library.
+ *
+ * The operation (paper Sec. 3, "Description of algorithm"; Sec. 3.1 "Input
+ * data"; Sec. 3.2 "Computations and data structure"): for every track, layer
+ * by layer, propagate the track state and its covariance along a helix in a
+ * uniform solenoidal field to the next detector surface -- a cylinder r = R
+ * ("p2r") or a plane z = Z ("p2z") -- and update the state with the one hit on
+ * that surface (three coordinates and a 3x3 covariance).  Propagation and
+ * update run as one fused GPU kernel over all tracks (Sec. 3.1).
+ *
+ * Conventions shared by every entry point
+ *   - Units: cm, GeV, T.  Field along +z.
+ *   - Track parameters p = (x, y, z, w, phi, theta): position, w = 1/pT > 0,
+ *     azimuth and polar angle of the momentum.  Charge q = +1 or -1, int32.
+ *     A positive charge bends clockwise seen from +z.
+ *   - Symmetric matrices are stored as their lower triangle, row-major:
+ *     (0,0),(1,0),(1,1),(2,0),(2,1),(2,2),...  A 6x6 covariance has 21
+ *     entries; a 3x3 hit covariance has 6: (xx, yx, yy, zx, zy, zz).
+ *   - Structure of arrays, track index fastest: component k of track t sits at
+ *     base[k * ld + t].  ld (the leading dimension, in elements) is >= the
+ *     number of tracks; pointers must be 16-byte aligned and ld a multiple of 4.
+ *   - Every data pointer is a DEVICE pointer owned by the caller, except where
+ *     an entry point says "host".  The library never frees caller memory.
+ *   - Calls are asynchronous on the caller's CUDA stream (a cudaStream_t passed
+ *     as void*, NULL = legacy default stream).  fit_sync waits and reports.
+ *   - Return value: FIT_OK (0) or a negative FIT_ERR_* code.  No exception or
+ *     abort crosses the ABI.  fit_last_error() describes the last failure on
+ *     the calling thread.
+ *   - Per-track problems never abort a call: they set a bit in the optional
+ *     per-track status byte and count into the handle's counters.
+ */
+#ifndef FIT_H_
+#define FIT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FIT_MAX_LAYERS 64
+
+/* Return codes. */
+#define FIT_OK 0
+#define FIT_ERR_ARG (-1)     /* invalid argument (pointer, size, alignment) */
+#define FIT_ERR_CUDA (-2)    /* a CUDA runtime call failed */
+#define FIT_ERR_TIMEOUT (-3) /* fit_sync gave up waiting */
+#define FIT_ERR_NOMEM (-4)   /* the library could not allocate its scratch */
+
+/* Per-track status bits. */
+#define FIT_ST_NO_INTERSECTION 1u /* the surface is not reached; the track stops
+                                     at its last good state */
+#define FIT_ST_NOT_CONVERGED 2u   /* p2r path-length iteration hit max_iter */
+#define FIT_ST_NONFINITE 4u       /* a non-finite value appeared; the track stops
+                                     and its outputs are unspecified */
+#define FIT_ST_CHARGE_FLIP 8u     /* an update made w negative: q and the sign of
+                                     w (and row/column 3 of C) were flipped */
+
+typedef enum { FIT_MODE_R = 0, FIT_MODE_Z = 1 } fit_mode;
+
+/* Geometry and numerics of one mode (p2r or p2z). */
+typedef struct {
+  float B;           /* field along +z [T] */
+  int nlayer;        /* number of surfaces, 1..FIT_MAX_LAYERS */
+  const float* surf; /* HOST pointer: nlayer radii (p2r) or z positions (p2z)
+                        [cm], in the order the tracks cross them; copied */
+  int max_iter;      /* p2r: maximum path-length iterations (<= 0: 10) */
+  float tol;         /* p2r: stop when a step is <= tol * R (<= 0: 1e-6) */
+} fit_config;
+
+typedef struct fit_handle fit_handle;
+
+/* Input tracks (read only). */
+typedef struct {
+  const float* par; /* [6][ld]  */
+  const float* cov; /* [21][ld] */
+  const int32_t* q; /* [ld]     */
+  int64_t ld;
+} fit_tracks_in;
+
+/* Output tracks.  par/cov/q may alias the inputs (in-place fit). */
+typedef struct {
+  float* par;        /* [6][ld]  fitted state after the last layer */
+  float* cov;        /* [21][ld] */
+  int32_t* q;        /* [ld]     */
+  float* chi2;       /* [ld]     sum over layers of the update chi2 */
+  float* chi2_layer; /* [nlayer][ld] per-layer chi2, or NULL */
+  uint8_t* status;   /* [ld]     FIT_ST_* bits, or NULL */
+  int64_t ld;
+} fit_tracks_out;
+
+/* Hits: one per track and layer (paper Sec. 3.1). */
+typedef struct {
+  const float* pos; /* [nlayer][3][ld]  x, y, z */
+  const float* cov; /* [nlayer][6][ld]  packed 3x3 */
+  int64_t ld;
+} fit_hits;
+
+/* What fit_sync reports: counters accumulated since the previous fit_sync. */
+typedef struct {
+  uint64_t tracks;          /* tracks processed */
+  uint64_t no_intersection; /* tracks with FIT_ST_NO_INTERSECTION */
+  uint64_t not_converged;   /* ... FIT_ST_NOT_CONVERGED */
+  uint64_t nonfinite;       /* ... FIT_ST_NONFINITE */
+  uint64_t charge_flip;     /* ... FIT_ST_CHARGE_FLIP */
+  uint64_t iterations;      /* p2r path-length iterations, summed over tracks
+                               and layers */
+} fit_status;
+
+/*
+ * fit_init: creates a handle on CUDA device `device` for the two modes.
+ * cfg_r / cfg_z describe the p2r cylinders and the p2z planes; either may be
+ * NULL if that mode is never used.  The handle allocates its own small device
+ * scratch (status counters) and frees it in fit_destroy.
+ * Errors: FIT_ERR_ARG (bad config), FIT_ERR_CUDA, FIT_ERR_NOMEM.
+ */
+int fit_init(fit_handle** h, const fit_config* cfg_r, const fit_config* cfg_z, int device);
+
+/*
+ * fit_propagate_update: the fused hot path (paper Sec. 3.1-3.2).  The tracks
+ * are nevt events stored one after another: event e holds ntrk[e] tracks
+ * (HOST array) and uses mode[e] (HOST array of fit_mode).  For every track
+ * and for l = 0..nlayer-1: propagate (p, C) to surface l of its mode, then
+ * update with hit l.  Track t of the concatenation reads in.par[k*in.ld + t],
+ * hits.pos[(l*3 + k)*hits.ld + t], ... and writes out.par[k*out.ld + t], ...
+ * nlayer must equal the configured nlayer of every mode used.
+ * Consecutive events of the same mode run as one kernel launch.
+ * Errors: FIT_ERR_ARG (NULL pointer, misaligned pointer or ld, sizes out of
+ * range, unconfigured mode), FIT_ERR_CUDA (launch failure).
+ */
+int fit_propagate_update(fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
+                         const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
+                         const int32_t* mode, void* stream);
+
+/*
+ * fit_sync: waits for the work queued by this handle on `stream`, then reads
+ * and clears the handle's counters into *st (st may be NULL).  timeout_s <= 0
+ * waits without limit; otherwise the wait polls and returns FIT_ERR_TIMEOUT
+ * after timeout_s seconds (the work is still queued; call again).
+ */
+int fit_sync(fit_handle* h, void* stream, double timeout_s, fit_status* st);
+
+/* fit_destroy: frees the handle and its scratch (after pending work ends). */
+void fit_destroy(fit_handle* h);
+
+/* fit_last_error: text of the last error on the calling thread ("" if none). */
+const char* fit_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIT_H_ */

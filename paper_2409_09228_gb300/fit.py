@@ -1,0 +1,227 @@
+"""Thin ctypes binding of libfit (include/fit.h), with the same names.
+
+Argument marshalling only: tensors are passed by data pointer, streams by
+handle; every step of the fit runs in the CUDA kernels of libfit.so.  There is
+no CPU fallback: if the library is missing or no GPU is present the calls
+raise.
+
+Layouts (track index fastest, see fit.h): par (6, ld), cov (21, ld), q (ld,)
+int32, chi2 (ld,), hit positions (nlayer, 3, ld), hit covariances
+(nlayer, 6, ld), all float32 CUDA tensors on the handle's device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+FIT_MODE_R = 0
+FIT_MODE_Z = 1
+FIT_OK = 0
+FIT_ERR_ARG = -1
+FIT_ERR_CUDA = -2
+FIT_ERR_TIMEOUT = -3
+FIT_ERR_NOMEM = -4
+FIT_ST_NO_INTERSECTION = 1
+FIT_ST_NOT_CONVERGED = 2
+FIT_ST_NONFINITE = 4
+FIT_ST_CHARGE_FLIP = 8
+FIT_MAX_LAYERS = 64
+
+
+class FitError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libfit error {code}: {msg}")
+        self.code = code
+
+
+class fit_config(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_float), ("nlayer", ctypes.c_int),
+                ("surf", ctypes.POINTER(ctypes.c_float)), ("max_iter", ctypes.c_int),
+                ("tol", ctypes.c_float)]
+
+
+class fit_tracks_in(ctypes.Structure):
+    _fields_ = [("par", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("q", ctypes.c_void_p),
+                ("ld", ctypes.c_int64)]
+
+
+class fit_tracks_out(ctypes.Structure):
+    _fields_ = [("par", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("q", ctypes.c_void_p),
+                ("chi2", ctypes.c_void_p), ("chi2_layer", ctypes.c_void_p),
+                ("status", ctypes.c_void_p), ("ld", ctypes.c_int64)]
+
+
+class fit_hits(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("ld", ctypes.c_int64)]
+
+
+class fit_status(ctypes.Structure):
+    _fields_ = [("tracks", ctypes.c_uint64), ("no_intersection", ctypes.c_uint64),
+                ("not_converged", ctypes.c_uint64), ("nonfinite", ctypes.c_uint64),
+                ("charge_flip", ctypes.c_uint64), ("iterations", ctypes.c_uint64)]
+
+
+EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_last_error")
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libfit.so (building it first if needed); raises if that fails."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfit.so not found at {path}; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    L.fit_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(fit_config),
+                           ctypes.POINTER(fit_config), ctypes.c_int]
+    L.fit_init.restype = ctypes.c_int
+    L.fit_propagate_update.argtypes = [vp, ctypes.POINTER(fit_tracks_in),
+                                       ctypes.POINTER(fit_tracks_out), ctypes.POINTER(fit_hits),
+                                       ctypes.c_int, ctypes.POINTER(i64), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int32), vp]
+    L.fit_propagate_update.restype = ctypes.c_int
+    L.fit_sync.argtypes = [vp, vp, ctypes.c_double, ctypes.POINTER(fit_status)]
+    L.fit_sync.restype = ctypes.c_int
+    L.fit_destroy.argtypes = [vp]
+    L.fit_destroy.restype = None
+    L.fit_last_error.argtypes = []
+    L.fit_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != FIT_OK:
+        raise FitError(code, load().fit_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return getattr(stream, "cuda_stream", stream) or None
+
+
+@dataclass
+class Geometry:
+    """One mode's surfaces: radii (p2r) or z positions (p2z) in cm, field in T."""
+    B: float
+    surf: Sequence[float]
+    max_iter: int = 10
+    tol: float = 1e-6
+
+
+def _config(g: Optional[Geometry]):
+    if g is None:
+        return None, None
+    arr = (ctypes.c_float * len(g.surf))(*[float(s) for s in g.surf])
+    return fit_config(float(g.B), len(g.surf), arr, int(g.max_iter), float(g.tol)), arr
+
+
+def fit_init(geom_r: Optional[Geometry], geom_z: Optional[Geometry], device: int = 0) -> int:
+    L = load()
+    h = ctypes.c_void_p()
+    cr, _keep_r = _config(geom_r)
+    cz, _keep_z = _config(geom_z)
+    _check(L.fit_init(ctypes.byref(h), ctypes.byref(cr) if cr else None,
+                      ctypes.byref(cz) if cz else None, int(device)))
+    return h.value
+
+
+def fit_propagate_update(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Sequence[int],
+                         mode: Sequence[int], par_out=None, cov_out=None, q_out=None, chi2=None,
+                         chi2_layer=None, status=None, stream=None) -> None:
+    """The fused fit on device tensors; outputs default to the inputs (in place)."""
+    L = load()
+    par_out = par_in if par_out is None else par_out
+    cov_out = cov_in if cov_out is None else cov_out
+    q_out = q_in if q_out is None else q_out
+    nlayer = hpos.shape[0]
+    tin = fit_tracks_in(_ptr(par_in), _ptr(cov_in), _ptr(q_in), par_in.shape[-1])
+    tout = fit_tracks_out(_ptr(par_out), _ptr(cov_out), _ptr(q_out), _ptr(chi2),
+                          _ptr(chi2_layer), _ptr(status), par_out.shape[-1])
+    hits = fit_hits(_ptr(hpos), _ptr(hcov), hpos.shape[-1])
+    nt = np.ascontiguousarray(ntrk, dtype=np.int64)
+    md = np.ascontiguousarray(mode, dtype=np.int32)
+    _check(L.fit_propagate_update(
+        ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
+        nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nlayer,
+        md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))
+
+
+def fit_sync(h: int, stream=None, timeout_s: float = 0.0) -> dict:
+    st = fit_status()
+    _check(load().fit_sync(ctypes.c_void_p(h), _stream_handle(stream), float(timeout_s),
+                           ctypes.byref(st)))
+    return {k: int(getattr(st, k)) for k, _ in fit_status._fields_}
+
+
+def fit_destroy(h: int) -> None:
+    if h:
+        load().fit_destroy(ctypes.c_void_p(h))
+
+
+def fit_last_error() -> str:
+    return load().fit_last_error().decode()
+
+
+class Fitter:
+    """Owns a handle; allocates output tensors; calls fit_propagate_update."""
+
+    def __init__(self, geom_r: Optional[Geometry], geom_z: Optional[Geometry], device: int = 0):
+        self.device = device
+        self.h = fit_init(geom_r, geom_z, device)
+        self.nlayer = len((geom_r or geom_z).surf)
+
+    def close(self):
+        if self.h:
+            fit_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, n: int, ld: Optional[int] = None, layers: bool = False):
+        import torch
+        ld = ld or (n + 3) // 4 * 4
+        dev = torch.device("cuda", self.device)
+        out = {"par": torch.empty((6, ld), device=dev), "cov": torch.empty((21, ld), device=dev),
+               "q": torch.empty((ld,), dtype=torch.int32, device=dev),
+               "chi2": torch.empty((ld,), device=dev),
+               "status": torch.empty((ld,), dtype=torch.uint8, device=dev)}
+        out["chi2_layer"] = torch.empty((self.nlayer, ld), device=dev) if layers else None
+        return out
+
+    def run(self, par, cov, q, hpos, hcov, ntrk, mode, out=None, layers=False, stream=None):
+        n = int(np.sum(ntrk))
+        out = out or self.outputs(n, ld=par.shape[-1], layers=layers)
+        fit_propagate_update(self.h, par, cov, q, hpos, hcov, ntrk, mode, par_out=out["par"],
+                             cov_out=out["cov"], q_out=out["q"], chi2=out["chi2"],
+                             chi2_layer=out["chi2_layer"], status=out["status"], stream=stream)
+        return out
+
+    def sync(self, stream=None, timeout_s: float = 0.0) -> dict:
+        return fit_sync(self.h, stream, timeout_s)

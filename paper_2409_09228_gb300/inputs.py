@@ -96,8 +96,12 @@ class TrackSet:
 def generate(mode: int, n: int, seed: int, nlayer: int = NLAYER, B: float = B_FIELD,
              surf: Optional[np.ndarray] = None, pt_range=(0.5, 10.0), eta_range=None,
              want_truth: bool = False, sigma_rphi: float = SIGMA_RPHI,
-             sigma_2: float = SIGMA_2) -> TrackSet:
-    """n independent tracks of one mode with hits on nlayer surfaces."""
+             sigma_2: float = SIGMA_2, pt: Optional[np.ndarray] = None) -> TrackSet:
+    """n independent tracks of one mode with hits on nlayer surfaces.
+
+    pt, if given, replaces the pT draw (and its p2r reach condition): hits on
+    cylinders a track cannot reach are NaN.
+    """
     surf = surfaces(mode, nlayer) if surf is None else np.asarray(surf, np.float32)
     nlayer = surf.shape[0]
     s64 = surf.astype(np.float64)
@@ -108,7 +112,8 @@ def generate(mode: int, n: int, seed: int, nlayer: int = NLAYER, B: float = B_FI
         eta_lo, eta_hi = (-1.0, 1.0) if eta_range is None else eta_range
     else:
         eta_lo, eta_hi = (1.5, 2.5) if eta_range is None else eta_range
-    pt = _rng(seed, _STREAM_PT).uniform(lo, hi, n)
+    pt_draw = _rng(seed, _STREAM_PT).uniform(lo, hi, n)
+    pt = pt_draw if pt is None else np.asarray(pt, np.float64)
     eta = _rng(seed, _STREAM_ETA).uniform(eta_lo, eta_hi, n)
     phi0 = _rng(seed, _STREAM_PHI).uniform(0.0, 2.0 * np.pi, n)
     q = np.where(_rng(seed, _STREAM_Q).random(n) < 0.5, -1, 1).astype(np.int32)
@@ -128,7 +133,8 @@ def generate(mode: int, n: int, seed: int, nlayer: int = NLAYER, B: float = B_FI
         if mode == MODE_R:
             # A circle through the origin reaches radius R after turning by
             # 2 asin(R / 2 rho); the crossing sits on the chord direction.
-            half = np.arcsin(s / (2.0 * rho))
+            with np.errstate(invalid="ignore"):
+                half = np.arcsin(s / (2.0 * rho))
             h = 2.0 * rho * half
             chord_phi = phi0 - q * half
             z = h * cot

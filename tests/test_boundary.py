@@ -1,0 +1,66 @@
+"""The C-ABI library loads and exports every function include/*.h declares (no GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2409_09228_gb300 import build as libbuild
+from paper_2409_09228_gb300 import fit
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(fit_\w+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not libbuild.up_to_date():
+        libbuild.build()
+    return ctypes.CDLL(libbuild.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_last_error"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_binding_names_match_header():
+    for name in declared_functions():
+        assert hasattr(fit, name), f"binding lacks {name}"
+
+
+def test_argument_errors_without_gpu(lib):
+    L = fit.load()
+    h = ctypes.c_void_p()
+    assert L.fit_init(None, None, None, 0) == fit.FIT_ERR_ARG
+    assert b"NULL" in L.fit_last_error()
+    assert L.fit_init(ctypes.byref(h), None, None, 0) == fit.FIT_ERR_ARG
+    assert L.fit_propagate_update(None, None, None, None, 0, None, 20, None, None) == fit.FIT_ERR_ARG
+    assert L.fit_sync(None, None, 0.0, None) == fit.FIT_ERR_ARG
+    L.fit_destroy(None)  # a no-op on NULL
+
+
+def test_struct_layouts_match_header():
+    # field offsets as a C compiler lays out the structs of fit.h (LP64)
+    assert ctypes.sizeof(fit.fit_config) == 24
+    assert fit.fit_config.surf.offset == 8
+    assert ctypes.sizeof(fit.fit_tracks_in) == 32
+    assert ctypes.sizeof(fit.fit_tracks_out) == 56
+    assert ctypes.sizeof(fit.fit_hits) == 24
+    assert ctypes.sizeof(fit.fit_status) == 48
