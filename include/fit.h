@@ -143,6 +143,45 @@ int fit_propagate_update(fit_handle* h, const fit_tracks_in* in, const fit_track
  */
 int fit_sync(fit_handle* h, void* stream, double timeout_s, fit_status* st);
 
+/*
+ * fit_propagate_update_noalloc: the same fused fit as fit_propagate_update,
+ * for callers that cannot allocate device memory.  (The paper has no
+ * counterpart; it is an addition of this library.)
+ *
+ * Who needs it: a process that reserves all of its GPU memory when it starts
+ * and must not allocate while it processes events -- an online trigger farm,
+ * for example -- or a plug-in running inside a host framework that owns the
+ * device memory.  fit_init allocates a counter block with cudaMalloc, so such
+ * callers cannot create a handle.  This entry point takes the geometry
+ * directly, allocates nothing (no cudaMalloc, no cudaFree, no allocating
+ * library call), and keeps its scratch -- per-event status counters and the
+ * event offsets -- in a fixed array compiled into the library: 192 KiB that
+ * every GPU which loads the library holds until the process exits.
+ *
+ * Arguments as fit_propagate_update, except:
+ *   cfg_r, cfg_z  geometry of the modes used (either may be NULL), as for
+ *                 fit_init; validated on every call.
+ *   nevt          at most FIT_NOALLOC_MAX_EVENTS; a larger value returns
+ *                 FIT_ERR_ARG without touching the GPU (split the events over
+ *                 several calls).
+ *   per_event     HOST array of nevt fit_status, or NULL.  If given, the call
+ *                 waits for its work on `stream` and fills entry e with the
+ *                 counts of event e (tracks = ntrk[e]).  If NULL the call
+ *                 returns as soon as its work is queued.
+ * The work runs on the current CUDA device.  The first call on a device looks
+ * up the device address of the fixed array (once per device); make that first
+ * call before any stream capture begins.  Every call shares the one array and
+ * each call clears the counters of its own events before its kernels run, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it: serialise them.
+ */
+#define FIT_NOALLOC_MAX_EVENTS 4096
+
+int fit_propagate_update_noalloc(const fit_config* cfg_r, const fit_config* cfg_z,
+                                 const fit_tracks_in* in, const fit_tracks_out* out,
+                                 const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
+                                 const int32_t* mode, void* stream, fit_status* per_event);
+
 /* fit_destroy: frees the handle and its scratch (after pending work ends). */
 void fit_destroy(fit_handle* h);
 

@@ -67,7 +67,9 @@ class fit_status(ctypes.Structure):
                 ("charge_flip", ctypes.c_uint64), ("iterations", ctypes.c_uint64)]
 
 
-EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_last_error")
+EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_last_error",
+           "fit_propagate_update_noalloc")
+FIT_NOALLOC_MAX_EVENTS = 4096
 
 _lib = None
 
@@ -102,6 +104,12 @@ def load(build_if_missing: bool = True):
     L.fit_destroy.restype = None
     L.fit_last_error.argtypes = []
     L.fit_last_error.restype = ctypes.c_char_p
+    L.fit_propagate_update_noalloc.argtypes = [
+        ctypes.POINTER(fit_config), ctypes.POINTER(fit_config), ctypes.POINTER(fit_tracks_in),
+        ctypes.POINTER(fit_tracks_out), ctypes.POINTER(fit_hits), ctypes.c_int,
+        ctypes.POINTER(i64), ctypes.c_int, ctypes.POINTER(ctypes.c_int32), vp,
+        ctypes.POINTER(fit_status)]
+    L.fit_propagate_update_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -167,6 +175,40 @@ def fit_propagate_update(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Sequenc
         ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
         nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nlayer,
         md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))
+
+
+def fit_propagate_update_noalloc(geom_r: Optional[Geometry], geom_z: Optional[Geometry], par_in,
+                                 cov_in, q_in, hpos, hcov, ntrk: Sequence[int],
+                                 mode: Sequence[int], par_out=None, cov_out=None, q_out=None,
+                                 chi2=None, chi2_layer=None, status=None, stream=None,
+                                 per_event: bool = True):
+    """The fused fit without a handle and without any allocation by the library.
+
+    For callers that must not allocate device memory while they run (see
+    fit.h).  Returns a list with one counter dict per event when per_event is
+    true (the call then waits for its work), else None.
+    """
+    L = load()
+    par_out = par_in if par_out is None else par_out
+    cov_out = cov_in if cov_out is None else cov_out
+    q_out = q_in if q_out is None else q_out
+    cr, _keep_r = _config(geom_r)
+    cz, _keep_z = _config(geom_z)
+    tin = fit_tracks_in(_ptr(par_in), _ptr(cov_in), _ptr(q_in), par_in.shape[-1])
+    tout = fit_tracks_out(_ptr(par_out), _ptr(cov_out), _ptr(q_out), _ptr(chi2),
+                          _ptr(chi2_layer), _ptr(status), par_out.shape[-1])
+    hits = fit_hits(_ptr(hpos), _ptr(hcov), hpos.shape[-1])
+    nt = np.ascontiguousarray(ntrk, dtype=np.int64)
+    md = np.ascontiguousarray(mode, dtype=np.int32)
+    st = (fit_status * max(1, len(nt)))() if per_event else None
+    _check(L.fit_propagate_update_noalloc(
+        ctypes.byref(cr) if cr else None, ctypes.byref(cz) if cz else None, ctypes.byref(tin),
+        ctypes.byref(tout), ctypes.byref(hits), len(nt),
+        nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), hpos.shape[0],
+        md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream), st))
+    if not per_event:
+        return None
+    return [{k: int(getattr(st[e], k)) for k, _ in fit_status._fields_} for e in range(len(nt))]
 
 
 def fit_sync(h: int, stream=None, timeout_s: float = 0.0) -> dict:
