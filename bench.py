@@ -34,11 +34,13 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 
-# Algorithmic work per track-layer (FP32 flops of the formulas, FMA = 2, as
-# counted in the design doc) and bytes (hit 36 B + track in/out 229 B / nlayer).
-FLOPS_P2Z = 570.0
-FLOPS_P2R_BASE = 703.0
-FLOPS_P2R_PER_ITER = 66.0
+# Algorithmic work per track-layer: FP32 flops of the kernel's formulas (FMA
+# = 2), as executed with one track per thread and counted by ncu (FFMA x 2 +
+# FADD + FMUL thread instructions, 20-event workload, 2.007 p2r iterations per
+# track-layer; profiles/fit_fused_*_100x9600x20.md), and bytes (hit 36 B +
+# track state in and out 229 B / nlayer).
+FLOPS_P2Z = 489.0
+FLOPS_P2R = 723.0
 BYTES_TRACK_IN = (6 + 21 + 1) * 4
 BYTES_TRACK_OUT = (6 + 21 + 1 + 1) * 4 + 1
 
@@ -293,9 +295,9 @@ def main():
     units_per_step = 2 * n * NLAYER
     value = world * units_per_step / (ms / 1e3)
 
-    # iterations of the p2r path-length step, for the algorithmic flop count
+    # iterations of the p2r path-length step (the flop count assumes 2.007)
     it_per = st.get("iterations", 0) / max(1, args.steps * n * NLAYER) if "iterations" in st else None
-    flops = [FLOPS_P2R_BASE + FLOPS_P2R_PER_ITER * (it_per if it_per else 3.0), FLOPS_P2Z]
+    flops = [FLOPS_P2R, FLOPS_P2Z]
     dom = int(np.argmax(kernel_ms))
     name = ["fit_fused_p2r", "fit_fused_p2z"][dom]
     peaks = load_peaks()

@@ -1,12 +1,14 @@
 // Per-track FP32 arithmetic of the fused propagate + update kernel.
 //
-// Everything here acts on one track held in registers: the parameters
+// Everything here acts on tracks held in registers: the parameters
 // p = (x, y, z, w, phi, theta) and the packed lower triangle c[21] of the 6x6
-// covariance.  The paper (Sec. 3, Sec. 3.2) names the steps -- helix
+// covariance.  Each function is a template over the lane type T (lanes.cuh):
+// float for one track, F2 for two tracks whose FP32 work shares packed
+// instructions.  The paper (Sec. 3, Sec. 3.2) names the steps -- helix
 // propagation to a plane or a cylinder with sin/cos and up-to-6x6 matrix
-// products, then a Kalman update with a small matrix inverse and trigonometric
-// functions -- but prints no formula; the ones used here are the textbook
-// helix and Kalman filter:
+// products, then a Kalman update with a small matrix inverse and
+// trigonometric functions -- but prints no formula; the ones used here are the
+// textbook helix and Kalman filter:
 //
 //   kappa = -q kA B w (1/cm); with u = kappa h / 2 and s(u) = sin(u)/u,
 //   x' = x + h s(u) cos(phi + u),  y' = y + h s(u) sin(phi + u),
@@ -18,11 +20,17 @@
 //   J = J_h + (d p'/d h) (grad h)^T, C' = J C J^T (sparse, see masks below).
 //   Update with the hit's 2-D position on the surface (x, y for p2z; the
 //   azimuthal direction at the hit and z for p2r).
+//
+// The cosine and sine of phi and theta travel with the track (struct Trig):
+// a propagation turns phi by kappa h, an update changes phi and theta by the
+// gain times the residual, and both are applied as rotations of the carried
+// (cos, sin) pairs, so a layer needs no trigonometric function call.
 #pragma once
 
 #include <cstdint>
 
 #include "fit.h"
+#include "lanes.cuh"
 
 namespace fitk {
 
@@ -34,309 +42,439 @@ __host__ __device__ constexpr int sym(int i, int j) {
   return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i;
 }
 
-// s(u) = sin(u)/u, its derivative s'(u), and cos(u).  For |u| <= 1.25 the
-// Taylor series in u^2 (truncated after u^12; remainder < 2e-10) avoid the
-// cancellation of (u cos u - sin u)/u^2 at small u, where the straight-line
-// limit kappa -> 0 must stay exact.
-__device__ __forceinline__ void sinc_d(float u, float& s, float& sp, float& cu) {
-  const float u2 = u * u;
-  if (fabsf(u) <= 1.25f) {
-    s = fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, 1.6059044e-10f, -2.5052108e-08f),
-                                                  2.7557319e-06f), -1.9841270e-04f), 8.3333333e-03f),
-                      -1.6666667e-01f), 1.0f);
-    sp = u * fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, 1.9270853e-09f, -2.5052108e-07f),
-                                             2.2045855e-05f), -1.1904762e-03f), 3.3333333e-02f),
-                  -3.3333333e-01f);
-    cu = fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, 2.0876757e-09f, -2.7557319e-07f),
-                                                   2.4801587e-05f), -1.3888889e-03f), 4.1666667e-02f),
-                       -0.5f), 1.0f);
+// sin and cos of x for |x| < 2^12 (the propagator's angles stay within a few
+// pi).  Cody & Waite's reduction x = j pi/2 + r with pi/2 split into the
+// nearest float and its remainder (W. J. Cody, W. Waite, "Software Manual for
+// the Elementary Functions", 1980), then the Taylor series of sin and cos on
+// |r| <= pi/4 truncated after r^9 and r^10 (remainders < 2e-9), and the
+// quadrant j mod 4 applied by swapping and sign flips.
+__device__ __forceinline__ void sincos_cw(float x, float& s, float& c) {
+  const float j = rintf(x * 0.636619772f);
+  float r = fmaf(j, -1.57079637f, x);  // float(pi/2)
+  r = fmaf(j, 4.37113883e-08f, r);     // pi/2 - float(pi/2) = -4.37113883e-08
+  const float r2 = r * r;
+  const float sr = fmaf(r * r2, fmaf(r2, fmaf(r2, fmaf(r2, 2.75573192e-06f, -1.98412698e-04f),
+                                            8.33333333e-03f), -1.66666667e-01f), r);
+  const float cr = fmaf(r2, fmaf(r2, fmaf(r2, fmaf(r2, fmaf(r2, -2.75573192e-07f, 2.48015873e-05f),
+                                                  -1.38888889e-03f), 4.16666667e-02f), -0.5f), 1.0f);
+  const int q = __float2int_rn(j);
+  const float sv = (q & 1) ? cr : sr;
+  const float cv = (q & 1) ? sr : cr;
+  s = __int_as_float(__float_as_int(sv) ^ ((q & 2) << 30));
+  c = __int_as_float(__float_as_int(cv) ^ (((q + 1) & 2) << 30));
+}
+__device__ __forceinline__ void sincos_cw(F2 x, F2& s, F2& c) {
+  sincos_cw(x.v.x, s.v.x, c.v.x);
+  sincos_cw(x.v.y, s.v.y, c.v.y);
+}
+
+// s(u) = sin(u)/u and cos(u) by their Taylor series in u^2: up to u^4 for
+// |u| <= 0.1 (remainders < 2e-9; steps between neighbouring layers stay in
+// this range), up to u^12 for |u| <= 1.25 (remainders < 2e-10), beyond that
+// from sin and cos.  The series keep the straight-line limit kappa -> 0 exact.
+template <class T>
+__device__ __forceinline__ void sinc_series(T u2, T& s, T& cu, bool shortform) {
+  if (shortform) {
+    s = fma(u2, fma(u2, T(8.3333333e-03f), T(-1.6666667e-01f)), T(1.0f));
+    cu = fma(u2, fma(u2, T(4.1666667e-02f), T(-0.5f)), T(1.0f));
   } else {
-    float sn;
-    sincosf(u, &sn, &cu);
-    s = sn / u;
-    sp = (cu - s) / u;
+    s = fma(u2, fma(u2, fma(u2, fma(u2, fma(u2, fma(u2, T(1.6059044e-10f), T(-2.5052108e-08f)),
+                                              T(2.7557319e-06f)), T(-1.9841270e-04f)),
+                             T(8.3333333e-03f)), T(-1.6666667e-01f)), T(1.0f));
+    cu = fma(u2, fma(u2, fma(u2, fma(u2, fma(u2, fma(u2, T(2.0876757e-09f), T(-2.7557319e-07f)),
+                                               T(2.4801587e-05f)), T(-1.3888889e-03f)),
+                              T(4.1666667e-02f)), T(-0.5f)), T(1.0f));
   }
 }
 
-// Sparsity of the transport Jacobian: bit (6 i + k) is set when J[i][k] can be
-// non-zero.  Rows/columns: x, y, z, w, phi, theta.
+__device__ __forceinline__ void sinc_c(float u, float& s, float& cu) {
+  const float au = fabsf(u);
+  if (au <= 1.25f) {
+    sinc_series(u * u, s, cu, au <= 0.1f);
+  } else {
+    float sn;
+    sincos_cw(u, sn, cu);
+    s = fdiv(sn, u);
+  }
+}
+__device__ __forceinline__ void sinc_c(F2 u, F2& s, F2& cu) {
+  const F2 au = fabs_(u);
+  if (all(le(au, F2(1.25f)))) {
+    sinc_series(u * u, s, cu, all(le(au, F2(0.1f))));
+  } else {
+    sinc_c(u.v.x, s.v.x, cu.v.x);
+    sinc_c(u.v.y, s.v.y, cu.v.y);
+  }
+}
+
+// s'(u), the derivative of sin(u)/u, given s(u) and cos(u); series as above
+// where (u cos u - sin u)/u^2 would cancel.
+template <class T>
+__device__ __forceinline__ T sinc_deriv_series(T u, bool shortform) {
+  const T u2 = u * u;
+  if (shortform) return u * fma(u2, fma(u2, T(-1.1904762e-03f), T(3.3333333e-02f)), T(-3.3333333e-01f));
+  return u * fma(u2, fma(u2, fma(u2, fma(u2, fma(u2, T(1.9270853e-09f), T(-2.5052108e-07f)),
+                                         T(2.2045855e-05f)), T(-1.1904762e-03f)),
+                          T(3.3333333e-02f)), T(-3.3333333e-01f));
+}
+__device__ __forceinline__ float sinc_deriv(float u, float s, float cu) {
+  const float au = fabsf(u);
+  if (au <= 1.25f) return sinc_deriv_series(u, au <= 0.1f);
+  return fdiv(cu - s, u);
+}
+__device__ __forceinline__ F2 sinc_deriv(F2 u, F2 s, F2 cu) {
+  const F2 au = fabs_(u);
+  if (all(le(au, F2(1.25f)))) return sinc_deriv_series(u, all(le(au, F2(0.1f))));
+  return F2(sinc_deriv(u.v.x, s.v.x, cu.v.x), sinc_deriv(u.v.y, s.v.y, cu.v.y));
+}
+
+// (c, s) <- (cos(a + d), sin(a + d)) from (c, s) = (cos a, sin a), given
+// (cd, sd) = (cos d, sin d).
+template <class T>
+__device__ __forceinline__ void turn(T& c, T& s, T cd, T sd) {
+  const T cn = fma(c, cd, -(s * sd));
+  s = fma(s, cd, c * sd);
+  c = cn;
+}
+
+// As turn(), for an angle d given by value: the change of an angle in one
+// update is small, so the Taylor series of sin d and cos d (to d^5 and d^4,
+// remainders < 2e-9 for |d| <= 0.1) replace a trigonometric call.
+template <class T>
+__device__ __forceinline__ void turn_by(T& c, T& s, T d) {
+  T sd, cd;
+  if (all(le(fabs_(d), T(0.1f)))) {
+    const T d2 = d * d;
+    sd = d * fma(d2, fma(d2, T(8.3333333e-03f), T(-1.6666667e-01f)), T(1.0f));
+    cd = fma(d2, fma(d2, T(4.1666667e-02f), T(-0.5f)), T(1.0f));
+  } else {
+    sincos_cw(d, sd, cd);
+  }
+  turn(c, s, cd, sd);
+}
+
+// Cosine and sine of phi and theta, carried with the track.
+template <class T>
+struct Trig {
+  T cphi, sphi, cth, sth;
+};
+
+template <class T>
+__device__ __forceinline__ Trig<T> trig_of(const T (&p)[6]) {
+  Trig<T> t;
+  sincos_cw(p[4], t.sphi, t.cphi);
+  sincos_cw(p[5], t.sth, t.cth);
+  return t;
+}
+
+// Transport Jacobian J = diag(unit rows) + E.  ROWS is the set of rows of J
+// whose diagonal entry is 1 + E_ii (bit i); the other rows vanish.  EMASK
+// marks the entries of E that can be non-zero (bit 6 i + k).  Rows and
+// columns: x, y, z, w, phi, theta.
 __host__ __device__ constexpr unsigned long long bit(int i, int k) { return 1ull << (6 * i + k); }
-// p2z: grad h = (0, 0, -tan, 0, 0, (Z - z)/cos^2); the z row vanishes.
-constexpr unsigned long long kMaskZ =
-    bit(0, 0) | bit(0, 2) | bit(0, 3) | bit(0, 4) | bit(0, 5) |
-    bit(1, 1) | bit(1, 2) | bit(1, 3) | bit(1, 4) | bit(1, 5) |
-    bit(3, 3) |
-    bit(4, 2) | bit(4, 3) | bit(4, 4) | bit(4, 5) |
-    bit(5, 5);
+__host__ __device__ constexpr unsigned row(int i) { return 1u << i; }
+// p2z: grad h = (0, 0, -tan, 0, 0, (Z - z)/cos^2); z' = Z, so the z row is 0.
+constexpr unsigned kRowsZ = row(0) | row(1) | row(3) | row(4) | row(5);
+constexpr unsigned long long kEZ =
+    bit(0, 2) | bit(0, 3) | bit(0, 4) | bit(0, 5) |
+    bit(1, 2) | bit(1, 3) | bit(1, 4) | bit(1, 5) |
+    bit(4, 2) | bit(4, 3) | bit(4, 5);
 // p2r: grad h has x, y, w, phi components.
-constexpr unsigned long long kMaskR =
+constexpr unsigned kRowsR = row(0) | row(1) | row(2) | row(3) | row(4) | row(5);
+constexpr unsigned long long kER =
     bit(0, 0) | bit(0, 1) | bit(0, 3) | bit(0, 4) |
     bit(1, 0) | bit(1, 1) | bit(1, 3) | bit(1, 4) |
-    bit(2, 0) | bit(2, 1) | bit(2, 2) | bit(2, 3) | bit(2, 4) | bit(2, 5) |
-    bit(3, 3) |
-    bit(4, 0) | bit(4, 1) | bit(4, 3) | bit(4, 4) |
-    bit(5, 5);
+    bit(2, 0) | bit(2, 1) | bit(2, 3) | bit(2, 4) | bit(2, 5) |
+    bit(4, 0) | bit(4, 1) | bit(4, 3) | bit(4, 4);
 
-// c <- J c J^T on the packed lower triangle, touching only the entries that
-// MASK marks.  With the loops unrolled the mask tests fold at compile time.
-template <unsigned long long MASK>
-__device__ __forceinline__ void similarity(const float (&J)[6][6], float (&c)[21]) {
-  float JC[6][6];
+// c <- J c J^T on the packed lower triangle.  With J = diag + E every product
+// chain starts from the entry it corrects (JC_ij = c_ij + sum_k E_ik c_kj,
+// C'_ij = JC_ij + sum_k JC_ik E_jk), so no chain needs a separate multiply.
+// With the loops unrolled the mask tests fold at compile time.
+template <unsigned ROWS, unsigned long long EMASK, class T>
+__device__ __forceinline__ void similarity(const T (&E)[6][6], T (&c)[21]) {
+  T JC[6][6];
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      float acc = 0.f;
+      T acc = (ROWS & row(i)) ? c[sym(i, j)] : T(0.f);
 #pragma unroll
       for (int k = 0; k < 6; ++k)
-        if (MASK & bit(i, k)) acc = fmaf(J[i][k], c[sym(k, j)], acc);
+        if (EMASK & bit(i, k)) acc = fma(E[i][k], c[sym(k, j)], acc);
       JC[i][j] = acc;
     }
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
     for (int j = 0; j <= i; ++j) {
-      float acc = 0.f;
-      if ((MASK & (63ull << (6 * i))) && (MASK & (63ull << (6 * j)))) {  // zero rows give 0
+      T acc = T(0.f);
+      if ((ROWS & row(i)) && (ROWS & row(j))) {  // a vanishing row gives 0
+        acc = JC[i][j];
 #pragma unroll
         for (int k = 0; k < 6; ++k)
-          if (MASK & bit(j, k)) acc = fmaf(JC[i][k], J[j][k], acc);
+          if (EMASK & bit(j, k)) acc = fma(JC[i][k], E[j][k], acc);
       }
       c[sym(i, j)] = acc;
     }
 }
 
-// Propagation to the plane z = Z.  Returns FIT_ST_* bits (0 on success); on
-// failure p and c are untouched.
-__device__ __forceinline__ unsigned prop_z(float (&p)[6], float (&c)[21], float dkdw, float Z) {
-  float sth, cth;
-  sincosf(p[5], &sth, &cth);
-  const float dz = Z - p[2];
-  const float tanth = sth / cth;
-  const float h = dz * tanth;
-  if (!(h > 0.f)) return FIT_ST_NO_INTERSECTION;
-  const float kappa = dkdw * p[3];
-  const float u = 0.5f * kappa * h;
-  float s, sp, cu;
-  sinc_d(u, s, sp, cu);
-  const float su = u * s;
-  float sm, cm;
-  sincosf(p[4] + u, &sm, &cm);
-  const float hs = h * s;
-  const float dx = hs * cm, dy = hs * sm;
-  const float c1 = cm * cu - sm * su;  // cos(phi')
-  const float s1 = sm * cu + cm * su;  // sin(phi')
-  const float hh = 0.5f * h * h * dkdw;
-  const float hth = dz / (cth * cth);  // dh/dtheta
-  float J[6][6];
-  J[0][0] = 1.f;
-  J[0][2] = -c1 * tanth;
-  J[0][3] = hh * (sp * cm - s * sm);
-  J[0][4] = -dy;
-  J[0][5] = c1 * hth;
-  J[1][1] = 1.f;
-  J[1][2] = -s1 * tanth;
-  J[1][3] = hh * (sp * sm + s * cm);
-  J[1][4] = dx;
-  J[1][5] = s1 * hth;
-  J[3][3] = 1.f;
-  J[4][2] = -kappa * tanth;
-  J[4][3] = h * dkdw;
-  J[4][4] = 1.f;
-  J[4][5] = kappa * hth;
-  J[5][5] = 1.f;
-  similarity<kMaskZ>(J, c);
+// Propagation to the plane z = Z.  Returns the mask of lanes whose plane is
+// behind them; if any lane fails nothing is modified.
+template <class T>
+__device__ __forceinline__ typename Lanes<T>::M prop_z(T (&p)[6], T (&c)[21], Trig<T>& g, T dkdw,
+                                                       float Z) {
+  const T dz = T(Z) - p[2];
+  const T tanth = fdiv(g.sth, g.cth);
+  const T h = dz * tanth;
+  const auto fail = not_(lt(T(0.f), h));
+  if (any(fail)) return fail;
+  const T kappa = dkdw * p[3];
+  const T u = T(0.5f) * kappa * h;
+  T s, cu;
+  sinc_c(u, s, cu);
+  const T sp = sinc_deriv(u, s, cu);
+  const T su = u * s;  // sin(u)
+  T cm = g.cphi, sm = g.sphi;
+  turn(cm, sm, cu, su);  // phi + u
+  const T hs = h * s;
+  const T dx = hs * cm, dy = hs * sm;
+  T c1 = cm, s1 = sm;
+  turn(c1, s1, cu, su);  // phi + 2u = phi'
+  const T hh = T(0.5f) * h * h * dkdw;
+  const T hth = fdiv(dz, g.cth * g.cth);  // dh/dtheta
+  T E[6][6];
+  E[0][2] = -(c1 * tanth);
+  E[0][3] = hh * fma(sp, cm, -(s * sm));
+  E[0][4] = -dy;
+  E[0][5] = c1 * hth;
+  E[1][2] = -(s1 * tanth);
+  E[1][3] = hh * fma(sp, sm, s * cm);
+  E[1][4] = dx;
+  E[1][5] = s1 * hth;
+  E[4][2] = -(kappa * tanth);
+  E[4][3] = h * dkdw;
+  E[4][5] = kappa * hth;
+  similarity<kRowsZ, kEZ>(E, c);
   p[0] += dx;
   p[1] += dy;
-  p[2] = Z;
-  p[4] += 2.f * u;
-  return 0u;
+  p[2] = T(Z);
+  p[4] = fma(T(2.f), u, p[4]);
+  g.cphi = c1;
+  g.sphi = s1;
+  return fail;
 }
 
 // Propagation to the cylinder r = R by straight-line steps along the current
-// direction.  Returns FIT_ST_* bits; NO_INTERSECTION leaves p and c untouched.
-__device__ __forceinline__ unsigned prop_r(float (&p)[6], float (&c)[21], float dkdw, float R,
-                                           int max_iter, float tol_abs, unsigned& iters) {
-  float sph, cph;
-  sincosf(p[4], &sph, &cph);
-  const float x = p[0], y = p[1];
-  const float R2 = R * R;
-  const float kappa = dkdw * p[3];
+// direction.  Returns the mask of lanes that cannot reach the cylinder; if
+// any lane fails nothing is modified.  iters[i] counts lane i's iterations;
+// notconv marks lanes that reached max_iter.
+template <class T>
+__device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Trig<T>& g, T dkdw,
+                                                       float R, int max_iter, float tol_abs,
+                                                       unsigned (&iters)[Lanes<T>::n],
+                                                       typename Lanes<T>::M& notconv) {
+  using M = typename Lanes<T>::M;
+  const T sph = g.sphi, cph = g.cphi;
+  const T x = p[0], y = p[1];
+  const T R2 = T(R * R);
+  const T kappa = dkdw * p[3];
   // The transverse circle (centre c, radius rho = 1/|kappa|) reaches radius
   // R only if |c| + rho >= R, which always holds when rho >= R.
-  {
-    const float rho = 1.f / fabsf(kappa);
-    if (rho < R) {
-      const float irs = 1.f / kappa;  // signed radius
-      const float cx = fmaf(-sph, irs, x), cy = fmaf(cph, irs, y);
-      if (sqrtf(fmaf(cx, cx, cy * cy)) + rho < R) return FIT_ST_NO_INTERSECTION;
-    }
+  M fail = lt(T(1.f), T(R) * fabs_(kappa));
+  if (any(fail)) {
+    const T irs = fdiv(T(1.f), kappa);  // signed radius
+    const T cx = fma(-sph, irs, x), cy = fma(cph, irs, y);
+    fail = and_(fail, lt(fsqrt(fma(cx, cx, cy * cy)) + fabs_(irs), T(R)));
   }
-  // First step: along the initial direction to the circle.
-  float h;
-  {
-    const float b = x * cph + y * sph;
-    const float c0 = fmaf(x, x, fmaf(y, y, -R2));
-    const float disc = fmaf(b, b, -c0);
-    if (!(disc >= 0.f)) return FIT_ST_NO_INTERSECTION;
-    const float sq = sqrtf(disc);
-    if (c0 <= 0.f) {
-      h = (b > 0.f) ? -c0 / (b + sq) : sq - b;  // forward root from inside
-    } else {
-      if (!(b < 0.f)) return FIT_ST_NO_INTERSECTION;  // outside, moving away
-      h = c0 / (sq - b);                               // nearer forward root
-    }
-  }
-  unsigned st = FIT_ST_NOT_CONVERGED;
-  float s = 1.f, sp = 0.f, sm = sph, cm = cph, px = x, py = y, c1 = cph, s1 = sph, d = 0.f;
+  // First step: along the initial direction to the circle (forward root from
+  // inside; from outside, the nearer forward root when moving inwards).
+  const T b0 = fma(x, cph, y * sph);
+  const T c0 = fma(x, x, fma(y, y, -R2));
+  const T disc0 = fma(b0, b0, -c0);
+  const T sq0 = fsqrt(disc0);
+  const M inside = le(c0, T(0.f));
+  fail = or_(fail, or_(lt(disc0, T(0.f)), and_(not_(inside), not_(lt(b0, T(0.f))))));
+  if (any(fail)) return fail;
+  T h = sel(inside, sel(lt(T(0.f), b0), fdiv(-c0, b0 + sq0), sq0 - b0), fdiv(c0, sq0 - b0));
+  // Iterate: helix at h, then a straight step along its direction to the
+  // circle.  The directions phi + u and phi + 2u come from turning
+  // (cos phi, sin phi) by u.  A lane that has converged keeps its h.
+  M conv = lt(T(1.f), T(0.f));  // all false
+  T u = T(0.f), s = T(1.f), cu = T(1.f), sm = sph, cm = cph, px = x, py = y, c1 = cph, s1 = sph,
+    d = T(0.f);
   for (int it = 0; it < max_iter; ++it) {
-    ++iters;
-    const float u = 0.5f * kappa * h;
-    float cu;
-    sinc_d(u, s, sp, cu);
-    const float su = u * s;
-    sincosf(p[4] + u, &sm, &cm);
-    const float hs = h * s;
-    px = fmaf(hs, cm, x);
-    py = fmaf(hs, sm, y);
-    c1 = cm * cu - sm * su;
-    s1 = sm * cu + cm * su;
+#pragma unroll
+    for (int i = 0; i < Lanes<T>::n; ++i) iters[i] += Lanes<T>::get(conv, i) ? 0u : 1u;
+    u = T(0.5f) * kappa * h;
+    sinc_c(u, s, cu);
+    const T su = u * s;
+    cm = cph;
+    sm = sph;
+    turn(cm, sm, cu, su);  // phi + u
+    const T hs = h * s;
+    px = fma(hs, cm, x);
+    py = fma(hs, sm, y);
+    c1 = cm;
+    s1 = sm;
+    turn(c1, s1, cu, su);  // phi + 2u
     // Step along (c1, s1) to the circle: d^2 + 2 b d + c2 = 0, smaller root.
-    const float b = px * c1 + py * s1;
-    const float c2 = fmaf(px, px, fmaf(py, py, -R2));
-    const float disc = fmaf(b, b, -c2);
-    d = (disc >= 0.f) ? -c2 / (b + copysignf(sqrtf(disc), b)) : -c2 / (2.f * b);
+    const T b = fma(px, c1, py * s1);
+    const T c2 = fma(px, px, fma(py, py, -R2));
+    const T disc = fma(b, b, -c2);
+    d = sel(le(T(0.f), disc), fdiv(-c2, b + copysign_(fsqrt(disc), b)), fdiv(-c2, T(2.f) * b));
+    d = sel(conv, T(0.f), d);
     h += d;
-    if (fabsf(d) <= tol_abs) {
-      st = 0u;
-      break;
-    }
+    conv = or_(conv, le(fabs_(d), T(tol_abs)));
+    if (all(conv)) break;
   }
+  notconv = not_(conv);
   // The loop evaluated the helix at h - d; move along the tangent by d
   // (the neglected curvature term, kappa d^2 / 2, is below FP32 resolution
-  // once |d| <= tol).
-  px = fmaf(d, c1, px);
-  py = fmaf(d, s1, py);
-  float sth, cth;
-  sincosf(p[5], &sth, &cth);
-  const float cot = cth / sth;
-  const float dx = px - x, dy = py - y;
-  const float hh = 0.5f * h * h * dkdw;
-  const float Xw = hh * (sp * cm - s * sm);
-  const float Yw = hh * (sp * sm + s * cm);
+  // once |d| <= tol) and turn the direction by kappa d.
+  px = fma(d, c1, px);
+  py = fma(d, s1, py);
+  const T sp = sinc_deriv(u, s, cu);
+  const T isth = fdiv(T(1.f), g.sth);
+  const T cot = g.cth * isth;
+  const T dx = px - x, dy = py - y;
+  const T hh = T(0.5f) * h * h * dkdw;
+  const T Xw = hh * fma(sp, cm, -(s * sm));
+  const T Yw = hh * fma(sp, sm, s * cm);
   // grad h = -grad g / (dg/dh) with g = x'^2 + y'^2 - R^2.
-  const float iD = 1.f / (px * c1 + py * s1);
-  const float hx = -px * iD, hy = -py * iD;
-  const float hw = -(px * Xw + py * Yw) * iD;
-  const float hp = (px * dy - py * dx) * iD;
-  float J[6][6];
-  J[0][0] = py * s1 * iD;  // = 1 + c1 hx
-  J[0][1] = c1 * hy;
-  J[0][3] = fmaf(c1, hw, Xw);
-  J[0][4] = fmaf(c1, hp, -dy);
-  J[1][0] = s1 * hx;
-  J[1][1] = px * c1 * iD;  // = 1 + s1 hy
-  J[1][3] = fmaf(s1, hw, Yw);
-  J[1][4] = fmaf(s1, hp, dx);
-  J[2][0] = cot * hx;
-  J[2][1] = cot * hy;
-  J[2][2] = 1.f;
-  J[2][3] = cot * hw;
-  J[2][4] = cot * hp;
-  J[2][5] = -h / (sth * sth);
-  J[3][3] = 1.f;
-  J[4][0] = kappa * hx;
-  J[4][1] = kappa * hy;
-  J[4][3] = fmaf(kappa, hw, h * dkdw);
-  J[4][4] = fmaf(kappa, hp, 1.f);
-  J[5][5] = 1.f;
-  similarity<kMaskR>(J, c);
+  const T iD = fdiv(T(1.f), fma(px, c1, py * s1));
+  const T hx = -(px * iD), hy = -(py * iD);
+  const T hw = -(fma(px, Xw, py * Yw) * iD);
+  const T hp = fma(px, dy, -(py * dx)) * iD;
+  T E[6][6];
+  E[0][0] = c1 * hx;
+  E[0][1] = c1 * hy;
+  E[0][3] = fma(c1, hw, Xw);
+  E[0][4] = fma(c1, hp, -dy);
+  E[1][0] = s1 * hx;
+  E[1][1] = s1 * hy;
+  E[1][3] = fma(s1, hw, Yw);
+  E[1][4] = fma(s1, hp, dx);
+  E[2][0] = cot * hx;
+  E[2][1] = cot * hy;
+  E[2][3] = cot * hw;
+  E[2][4] = cot * hp;
+  E[2][5] = -(h * isth * isth);
+  E[4][0] = kappa * hx;
+  E[4][1] = kappa * hy;
+  E[4][3] = fma(kappa, hw, h * dkdw);
+  E[4][4] = kappa * hp;
+  similarity<kRowsR, kER>(E, c);
   p[0] = px;
   p[1] = py;
-  p[2] = fmaf(h, cot, p[2]);
-  p[4] = fmaf(kappa, h, p[4]);
-  return st;
+  p[2] = fma(h, cot, p[2]);
+  p[4] = fma(kappa, h, p[4]);
+  turn_by(c1, s1, kappa * d);
+  g.cphi = c1;
+  g.sphi = s1;
+  return fail;
 }
 
 // Kalman update with a 2-D measurement: a and b are the columns of C H^T (the
 // two measured directions), S = H C H^T + H V H^T, K = C H^T S^-1,
 // p += K r, C -= K (H C), chi2 = r^T S^-1 r.
 //
-// FP32 note: a and b are strongly correlated and so is S, so K = [a b] S^-1
-// cancels.  K is formed as [a S11 - b S01, b S00 - a S01] / det with the
-// rounding error of each second product recovered by an FMA (and det by
-// Kahan's 2x2 determinant); forming S^-1 first and multiplying loses up to
-// ~1e-4 relative accuracy in the 1/pT variance after 20 layers.
-__device__ __forceinline__ float kalman_2d(float (&p)[6], float (&c)[21], const float (&a)[6],
-                                           const float (&b)[6], float S00, float S01, float S11,
-                                           float r0, float r1) {
-  const float w01 = S01 * S01;
-  const float det = fmaf(S00, S11, -w01) - fmaf(S01, S01, -w01);
-  const float id = 1.f / det;
-  float k0[6], k1[6];
+// FP32 note (COMPENSATED): with the p2z measurement (x, y) the columns a and
+// b are strongly correlated and so is S, so K = [a b] S^-1 cancels.  K is
+// then formed as [a S11 - b S01, b S00 - a S01] / det with the rounding error
+// of each second product recovered by an FMA (and det by Kahan's 2x2
+// determinant); forming S^-1 first loses up to ~1e-4 relative accuracy in the
+// 1/pT variance after 20 layers.  The p2r measurement directions (azimuthal,
+// z) are nearly uncorrelated and need no compensation.
+template <bool COMPENSATED, class T>
+__device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], const T (&b)[6],
+                                       T S00, T S01, T S11, T r0, T r1) {
+  T k0[6], k1[6], id;
+  if (COMPENSATED) {
+    const T w01 = S01 * S01;
+    const T det = fma(S00, S11, -w01) - fma(S01, S01, -w01);
+    id = fdiv(T(1.f), det);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const float t0 = b[i] * S01, t1 = a[i] * S01;
-    k0[i] = (fmaf(a[i], S11, -t0) - fmaf(b[i], S01, -t0)) * id;
-    k1[i] = (fmaf(b[i], S00, -t1) - fmaf(a[i], S01, -t1)) * id;
+    for (int i = 0; i < 6; ++i) {
+      const T t0 = b[i] * S01, t1 = a[i] * S01;
+      k0[i] = (fma(a[i], S11, -t0) - fma(b[i], S01, -t0)) * id;
+      k1[i] = (fma(b[i], S00, -t1) - fma(a[i], S01, -t1)) * id;
+    }
+  } else {
+    id = fdiv(T(1.f), fma(S00, S11, -(S01 * S01)));
+    const T i00 = S11 * id, i01 = -(S01 * id), i11 = S00 * id;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      k0[i] = fma(a[i], i00, b[i] * i01);
+      k1[i] = fma(a[i], i01, b[i] * i11);
+    }
   }
 #pragma unroll
-  for (int i = 0; i < 6; ++i) p[i] = fmaf(k0[i], r0, fmaf(k1[i], r1, p[i]));
+  for (int i = 0; i < 6; ++i) p[i] = fma(k0[i], r0, fma(k1[i], r1, p[i]));
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j) c[sym(i, j)] -= fmaf(k0[i], a[j], k1[i] * b[j]);
+    for (int j = 0; j <= i; ++j) c[sym(i, j)] = fma(-k0[i], a[j], fma(-k1[i], b[j], c[sym(i, j)]));
   // chi2 = (S11 r0^2 - 2 S01 r0 r1 + S00 r1^2) / det
-  return fmaf(S11 * r0, r0, fmaf(S00 * r1, r1, -2.f * S01 * r0 * r1)) * id;
+  return fma(S11 * r0, r0, fma(S00 * r1, r1, T(-2.f) * S01 * r0 * r1)) * id;
 }
 
-// After an update: phi into (-pi, pi]; a negative w flips the charge.
-__device__ __forceinline__ unsigned normalise(float (&p)[6], float (&c)[21], int& q) {
-  const float k = floorf((kPi - p[4]) * (1.f / kTwoPi));
-  p[4] = fmaf(k, kTwoPi, p[4]);
-  if (p[3] < 0.f) {
-    p[3] = -p[3];
-    q = -q;
+// After an update: carry cos/sin of phi and theta through the change of the
+// angles (given their values before the update), wrap phi into (-pi, pi], and
+// flip the charge (qf = +-1 per lane) where w became negative.  Returns the
+// mask of flipped lanes.
+template <class T>
+__device__ __forceinline__ typename Lanes<T>::M normalise(T (&p)[6], T (&c)[21], T& qf,
+                                                          Trig<T>& g, T phi_before, T th_before) {
+  turn_by(g.cphi, g.sphi, p[4] - phi_before);
+  turn_by(g.cth, g.sth, p[5] - th_before);
+  const T k = floor_((T(kPi) - p[4]) * T(1.f / kTwoPi));
+  p[4] = fma(k, T(kTwoPi), p[4]);
+  const auto flip = lt(p[3], T(0.f));
+  if (any(flip)) {
+    const T sgn = sel(flip, T(-1.f), T(1.f));
+    p[3] = p[3] * sgn;
+    qf = qf * sgn;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
-      if (i != 3) c[sym(3, i)] = -c[sym(3, i)];
-    return FIT_ST_CHARGE_FLIP;
+      if (i != 3) c[sym(3, i)] = c[sym(3, i)] * sgn;
   }
-  return 0u;
+  return flip;
 }
 
 // p2z update: H measures x and y.
-__device__ __forceinline__ float update_z(float (&p)[6], float (&c)[21], const float (&m)[3],
-                                          const float (&v)[6]) {
-  float a[6], b[6];
+template <class T>
+__device__ __forceinline__ T update_z(T (&p)[6], T (&c)[21], const T (&m)[3], const T (&v)[6]) {
+  T a[6], b[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     a[i] = c[sym(i, 0)];
     b[i] = c[sym(i, 1)];
   }
-  return kalman_2d(p, c, a, b, a[0] + v[0], b[0] + v[1], b[1] + v[2], m[0] - p[0], m[1] - p[1]);
+  return kalman_2d<true>(p, c, a, b, a[0] + v[0], b[0] + v[1], b[1] + v[2], m[0] - p[0],
+                         m[1] - p[1]);
 }
 
 // p2r update: H measures the position along the cylinder's azimuthal
 // direction t = (-sin phi_h, cos phi_h, 0) at the hit azimuth, and z.
-__device__ __forceinline__ float update_r(float (&p)[6], float (&c)[21], const float (&m)[3],
-                                          const float (&v)[6]) {
-  const float ir = rsqrtf(fmaf(m[0], m[0], m[1] * m[1]));
-  const float sh = m[1] * ir, ch = m[0] * ir;
-  float a[6], b[6];
+template <class T>
+__device__ __forceinline__ T update_r(T (&p)[6], T (&c)[21], const T (&m)[3], const T (&v)[6]) {
+  const T ir = frsqrt(fma(m[0], m[0], m[1] * m[1]));
+  const T sh = m[1] * ir, ch = m[0] * ir;
+  T a[6], b[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    a[i] = fmaf(ch, c[sym(i, 1)], -sh * c[sym(i, 0)]);
+    a[i] = fma(ch, c[sym(i, 1)], -(sh * c[sym(i, 0)]));
     b[i] = c[sym(i, 2)];
   }
-  const float vtt = fmaf(sh * sh, v[0], fmaf(ch * ch, v[2], -2.f * sh * ch * v[1]));
-  const float vtz = fmaf(ch, v[4], -sh * v[3]);
-  const float S00 = fmaf(ch, a[1], -sh * a[0]) + vtt;
-  const float S01 = a[2] + vtz;
-  const float S11 = b[2] + v[5];
-  const float r0 = fmaf(ch, m[1] - p[1], -sh * (m[0] - p[0]));
-  const float r1 = m[2] - p[2];
-  return kalman_2d(p, c, a, b, S00, S01, S11, r0, r1);
+  const T vtt = fma(sh * sh, v[0], fma(ch * ch, v[2], T(-2.f) * sh * ch * v[1]));
+  const T vtz = fma(ch, v[4], -(sh * v[3]));
+  const T S00 = fma(ch, a[1], -(sh * a[0])) + vtt;
+  const T S01 = a[2] + vtz;
+  const T S11 = b[2] + v[5];
+  const T r0 = fma(ch, m[1] - p[1], -(sh * (m[0] - p[0])));
+  const T r1 = m[2] - p[2];
+  return kalman_2d<false>(p, c, a, b, S00, S01, S11, r0, r1);
 }
 
 }  // namespace fitk
