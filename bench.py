@@ -226,6 +226,73 @@ def config_dict(args):
             "l2": "inputs larger than L2 (691 MB of hits per mode per step); no flush"}
 
 
+def bench_uneven(args, world, rank, local):
+    """2000 events, log-normal track counts (median 2000, sigma 1, clipped
+    50..20000), p2r or p2z at random per event, 20 layers: the per-segment
+    path (one launch per run of same-mode events) against the batched
+    persistent plan (one launch under a CUDA graph), default and autotuned."""
+    import torch
+    from paper_2409_09228_gb300 import fit, inputs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nevt = args.uneven_events
+    nt = inputs.uneven_event_sizes(nevt, 3)
+    md = inputs.uneven_event_modes(nevt, 3)
+    ev = inputs.generate_events(nt, md, seed=3 + 1000 * rank)
+    n = ev.n
+    ld = (n + 3) // 4 * 4
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(np.pad(a, [(0, 0)] * (a.ndim - 1) + [(0, ld - n)]))).to(dev)  # noqa: E731
+    dev_in = [up(a) for a in (ev.par0, ev.cov0, ev.q, ev.hpos, ev.hcov)]
+    del ev.hpos, ev.hcov
+    f = fit.Fitter(fit.Geometry(ev.B, ev.surf[0]), fit.Geometry(ev.B, ev.surf[1]), device=local)
+    out = f.outputs(n, ld=ld)
+    stream = torch.cuda.current_stream(dev)
+    bufs = dict(par_out=out["par"], cov_out=out["cov"], q_out=out["q"], chi2=out["chi2"],
+                status=out["status"])
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
+
+    seg_ms = timed(lambda: f.run(*dev_in, nt, md, out=out, stream=stream))
+    plan = fit.fit_plan_create(f.h, nt, md, NLAYER)
+    plan_ms = timed(lambda: fit.fit_plan_run(plan, *dev_in, stream=stream, **bufs))
+    info_default = fit.fit_plan_get_info(plan)
+    info = fit.fit_plan_tune(plan, *dev_in, stream=stream, **bufs)
+    tuned_ms = timed(lambda: fit.fit_plan_run(plan, *dev_in, stream=stream, **bufs))
+    st = f.sync(stream)
+    assert st["nonfinite"] == 0 and st["no_intersection"] == 0, st
+    fit.fit_plan_destroy(plan)
+    f.close()
+    if rank != 0:
+        return
+    units = world * n * NLAYER
+    segments = int(1 + np.count_nonzero(np.diff(md)))
+    line = {"metric": "track-layer propagate+update/s", "value": units / (tuned_ms / 1e3),
+            "unit": "track-layer/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tuned_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"uneven batch: {nevt} events, log-normal track counts "
+                                   f"(median 2000, sigma 1, 50..20000), p2r/p2z per event, "
+                                   f"{NLAYER} layers", "tracks": n, "events": nevt,
+                       "same_mode_runs": segments},
+            "per_segment_launches": {"ms": seg_ms, "launches": segments,
+                                     "value": units / (seg_ms / 1e3)},
+            "plan_default": {"ms": plan_ms, "value": units / (plan_ms / 1e3), **info_default},
+            "plan_tuned": {"ms": tuned_ms, **info}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -235,12 +302,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--nevt", type=int, default=NEVT, help="events per mode (default 100)")
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven"],
+                    help="uniform: 100 x 9600 x 20 per mode (the default); uneven: the batched "
+                         "form on 2000 events of log-normal size and mixed modes")
+    ap.add_argument("--uneven-events", type=int, default=2000)
     args = ap.parse_args()
     set_nevt(args.nevt)
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "uneven":
+        bench_uneven(args, world, rank, local)
         return
 
     import torch

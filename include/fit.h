@@ -182,6 +182,70 @@ int fit_propagate_update_noalloc(const fit_config* cfg_r, const fit_config* cfg_
                                  const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
                                  const int32_t* mode, void* stream, fit_status* per_event);
 
+/*
+ * Batched form (many events of uneven size and mixed modes in one launch).
+ *
+ * A plan fixes the event structure (ntrk[], mode[], nlayer) once.  Its work is
+ * cut into items -- tiles of one event, 2 x threads_per_block tracks -- that a
+ * persistent kernel's blocks pull from a counter until none is left, so the
+ * uneven events and the two surface types share one launch.  fit_plan_run
+ * captures that launch (and the counter reset) in a CUDA graph the first time
+ * it sees a set of buffers and replays the graph afterwards.  The results are
+ * those of fit_propagate_update on the same events.
+ */
+typedef struct {
+  int threads_per_block; /* 64 or 128 (two tracks per thread) */
+  int blocks_per_sm;     /* grid = blocks_per_sm x SM count; 0 = as many as fit */
+  int persistent;        /* 1: one persistent launch; 0: one launch per run of
+                            same-mode events (fit_propagate_update's form) */
+} fit_launch_config;
+
+typedef struct {
+  fit_launch_config config; /* the launch shape the plan runs with */
+  int64_t tracks;           /* tracks in the plan */
+  int32_t items;            /* work items of the persistent form */
+  int32_t tuned;            /* 0: default or given; 1: measured by fit_plan_tune;
+                               2: taken from the tuning cache */
+  float best_ms;            /* fit_plan_tune: time of the chosen shape, else 0 */
+} fit_plan_info;
+
+typedef struct fit_plan fit_plan;
+
+/*
+ * fit_plan_create: a plan for nevt events (ntrk, mode: HOST arrays, copied).
+ * cfg may be NULL (persistent, 128 threads per block, as many blocks per SM
+ * as fit).  The plan allocates its work-item table and a counter on the
+ * handle's device.  Errors: FIT_ERR_ARG, FIT_ERR_NOMEM, FIT_ERR_CUDA.
+ */
+int fit_plan_create(fit_handle* h, int nevt, const int64_t* ntrk, const int32_t* mode, int nlayer,
+                    const fit_launch_config* cfg, fit_plan** plan);
+
+/*
+ * fit_plan_run: the fused fit of the plan's events on these buffers (layouts
+ * as fit_propagate_update), asynchronous on `stream`; counts into the handle's
+ * counters (fit_sync).
+ */
+int fit_plan_run(fit_plan* plan, const fit_tracks_in* in, const fit_tracks_out* out,
+                 const fit_hits* hits, void* stream);
+
+/*
+ * fit_plan_tune: the autotuner.  Times every candidate launch shape (persistent
+ * with 64 or 128 threads per block at each resident-block count, and the
+ * per-segment form) on these buffers -- out must not alias in, it is written --
+ * and keeps the fastest.  A shape found before for the same device, depth and
+ * event-size histogram (in this process, or in the text file cache_path if not
+ * NULL) is reused without measuring; new results are appended to cache_path.
+ * Waits for the stream.  The tuning runs do not count into the handle.
+ */
+int fit_plan_tune(fit_plan* plan, const fit_tracks_in* in, const fit_tracks_out* out,
+                  const fit_hits* hits, void* stream, const char* cache_path);
+
+/* fit_plan_get_info: the plan's launch shape and sizes. */
+int fit_plan_get_info(const fit_plan* plan, fit_plan_info* info);
+
+/* fit_plan_destroy: frees the plan (after its pending work ends). */
+void fit_plan_destroy(fit_plan* plan);
+
 /* fit_destroy: frees the handle and its scratch (after pending work ends). */
 void fit_destroy(fit_handle* h);
 

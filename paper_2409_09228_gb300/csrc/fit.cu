@@ -1,12 +1,7 @@
-// libfit: the fused propagate + Kalman-update kernels and the C ABI of fit.h.
-//
-// One thread owns one track for all layers (paper Sec. 3.1: propagation and
-// update in one kernel; Sec. 4.2: per-track intermediates kept in registers).
-// Track state and covariance are loaded once, stay in registers through every
-// layer, and are stored once.  The hits of layer l+1 are loaded while layer l
-// is computed; consecutive threads read consecutive words of each hit
-// component (structure of arrays, track index fastest), so every load of a
-// warp is one 128-byte line.
+// libfit: the fused propagate + Kalman-update kernels over runs of same-mode
+// events, and the C ABI of fit.h (handle, fit_propagate_update,
+// fit_propagate_update_noalloc, fit_sync).  The batched persistent form is in
+// batch.cu.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -17,9 +12,9 @@
 #include <thread>
 
 #include "fit.h"
-#include "track_math.cuh"
+#include "fused.cuh"
 
-namespace {
+namespace fitimpl {
 
 thread_local std::string g_last_error;
 
@@ -32,261 +27,17 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(FIT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-constexpr int kBlock = 128;
-constexpr int kCounters = 5;  // no_intersection, not_converged, nonfinite, charge_flip,
-                               // p2r path-length iterations
-
-struct Surfaces {
-  float s[FIT_MAX_LAYERS];
-};
-
-struct FitArgs {
-  const float* par_in;
-  const float* cov_in;
-  const int32_t* q_in;
-  int64_t ld_in;
-  float* par_out;
-  float* cov_out;
-  int32_t* q_out;
-  float* chi2;
-  float* chi2_layer;
-  uint8_t* status;
-  int64_t ld_out;
-  const float* hpos;
-  const float* hcov;
-  int64_t ld_hit;
-  int64_t t0, t1;  // track range [t0, t1)
-  int nlayer;
-  float kB;        // kA * B
-  int max_iter;
-  float tol;
-  unsigned long long* counters;
-  Surfaces surf;
-};
-
-__device__ __forceinline__ void count_status(unsigned st, unsigned long long* counters) {
-  if (st & FIT_ST_NO_INTERSECTION) atomicAdd(&counters[0], 1ull);
-  if (st & FIT_ST_NOT_CONVERGED) atomicAdd(&counters[1], 1ull);
-  if (st & FIT_ST_NONFINITE) atomicAdd(&counters[2], 1ull);
-  if (st & FIT_ST_CHARGE_FLIP) atomicAdd(&counters[3], 1ull);
-}
-
-using fitk::F2;
-using fitk::Lanes;
-
-// One or two tracks (lane type T) in registers for the whole layer loop.
-template <class T>
-struct State {
-  T p[6], c[21];
-  T qf;    // charge as +-1.f
-  T chi2;  // sum over layers
-  fitk::Trig<T> g;
-};
-
-template <class T>
-__device__ __forceinline__ void load_state(const FitArgs& a, int64_t t, State<T>& s);
-template <>
-__device__ __forceinline__ void load_state(const FitArgs& a, int64_t t, State<float>& s) {
-#pragma unroll
-  for (int k = 0; k < 6; ++k) fitk::ld(s.p[k], a.par_in + k * a.ld_in + t);
-#pragma unroll
-  for (int k = 0; k < 21; ++k) fitk::ld(s.c[k], a.cov_in + k * a.ld_in + t);
-  s.qf = (float)__ldcs(a.q_in + t);
-  s.chi2 = 0.f;
-  s.g = fitk::trig_of(s.p);
-}
-template <>
-__device__ __forceinline__ void load_state(const FitArgs& a, int64_t t, State<F2>& s) {
-#pragma unroll
-  for (int k = 0; k < 6; ++k) fitk::ld(s.p[k], a.par_in + k * a.ld_in + t);
-#pragma unroll
-  for (int k = 0; k < 21; ++k) fitk::ld(s.c[k], a.cov_in + k * a.ld_in + t);
-  const int2 q = __ldcs(reinterpret_cast<const int2*>(a.q_in + t));
-  s.qf = F2((float)q.x, (float)q.y);
-  s.chi2 = F2(0.f);
-  s.g = fitk::trig_of(s.p);
-}
-
-// Lane i of a two-track state as a one-track state.
-__device__ __forceinline__ State<float> lane_of(const State<F2>& s, int i) {
-  State<float> r;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) r.p[k] = Lanes<F2>::get(s.p[k], i);
-#pragma unroll
-  for (int k = 0; k < 21; ++k) r.c[k] = Lanes<F2>::get(s.c[k], i);
-  r.qf = Lanes<F2>::get(s.qf, i);
-  r.chi2 = Lanes<F2>::get(s.chi2, i);
-  r.g = {Lanes<F2>::get(s.g.cphi, i), Lanes<F2>::get(s.g.sphi, i), Lanes<F2>::get(s.g.cth, i),
-         Lanes<F2>::get(s.g.sth, i)};
-  return r;
-}
-
-// Writes the outputs of the lanes of s (tracks t, t+1, ...), after the final
-// finiteness check.
-template <class T>
-__device__ __forceinline__ void store_state(const FitArgs& a, int64_t t, const State<T>& s,
-                                            unsigned (&st)[Lanes<T>::n]) {
-  auto fin = fitk::finite_(s.chi2);
-#pragma unroll
-  for (int k = 0; k < 6; ++k) fin = fitk::and_(fin, fitk::finite_(s.p[k]));
-#pragma unroll
-  for (int k = 0; k < 21; ++k) fin = fitk::and_(fin, fitk::finite_(s.c[k]));
-#pragma unroll
-  for (int i = 0; i < Lanes<T>::n; ++i)
-    if (!Lanes<T>::get(fin, i)) st[i] |= FIT_ST_NONFINITE;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) fitk::st(a.par_out + k * a.ld_out + t, s.p[k]);
-#pragma unroll
-  for (int k = 0; k < 21; ++k) fitk::st(a.cov_out + k * a.ld_out + t, s.c[k]);
-  fitk::st(a.chi2 + t, s.chi2);
-#pragma unroll
-  for (int i = 0; i < Lanes<T>::n; ++i) {
-    a.q_out[t + i] = (int32_t)Lanes<T>::get(s.qf, i);
-    if (a.status) a.status[t + i] = (uint8_t)st[i];
-  }
-}
-
-// The fused layer loop (paper Sec. 3.1: propagate to the next layer, update
-// with its hit) for the lanes of s, tracks t, t+1, ..., from layer l0.
-// MODE selects the surface type at compile time.  Returns the layer whose
-// surface some live lane cannot reach (its propagation is not applied), or
-// nlayer.  A lane whose update turns non-finite stops (alive false); its
-// later per-layer chi2 entries are 0.
-template <int MODE, class T>
-__device__ __forceinline__ int run_layers(const FitArgs& a, int64_t t, int l0, State<T>& s,
-                                          unsigned (&st)[Lanes<T>::n],
-                                          unsigned (&iters)[Lanes<T>::n],
-                                          typename Lanes<T>::M& alive) {
-  using M = typename Lanes<T>::M;
-  const float* hp = a.hpos + t;
-  const float* hc = a.hcov + t;
-  const int64_t ldh = a.ld_hit;
-  for (int l = l0; l < a.nlayer; ++l) {
-    T m[3], v[6];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) fitk::ld(m[k], hp + (3 * l + k) * ldh);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) fitk::ld(v[k], hc + (6 * l + k) * ldh);
-    const float sf = a.surf.s[l];
-    const T dkdw = s.qf * T(-a.kB);
-    M fail, nc = fitk::lt(T(1.f), T(0.f));
-    if (MODE == FIT_MODE_Z)
-      fail = fitk::prop_z(s.p, s.c, s.g, dkdw, sf);
-    else
-      fail = fitk::prop_r(s.p, s.c, s.g, dkdw, sf, a.max_iter, a.tol * sf, iters, nc);
-    if (fitk::any(fitk::and_(fail, alive))) return l;
-    const T phi_pred = s.p[4], th_pred = s.p[5];
-    T x2 = (MODE == FIT_MODE_Z) ? fitk::update_z(s.p, s.c, m, v) : fitk::update_r(s.p, s.c, m, v);
-    const M flip = fitk::normalise(s.p, s.c, s.qf, s.g, phi_pred, th_pred);
-    alive = fitk::and_(alive, fitk::finite_(x2));
-#pragma unroll
-    for (int i = 0; i < Lanes<T>::n; ++i) {
-      if (Lanes<T>::get(nc, i)) st[i] |= FIT_ST_NOT_CONVERGED;
-      if (Lanes<T>::get(flip, i)) st[i] |= FIT_ST_CHARGE_FLIP;
-      if (!Lanes<T>::get(alive, i)) st[i] |= FIT_ST_NONFINITE;
-    }
-    x2 = fitk::sel(alive, x2, T(0.f));
-    s.chi2 += x2;
-    if (a.chi2_layer) fitk::st(a.chi2_layer + (int64_t)l * a.ld_out + t, x2);
-    if (!fitk::any(alive)) {
-      if (a.chi2_layer)
-        for (int r = l + 1; r < a.nlayer; ++r) fitk::st(a.chi2_layer + (int64_t)r * a.ld_out + t, T(0.f));
-      return a.nlayer;
-    }
-  }
-  return a.nlayer;
-}
-
-// One track alone from layer l0 to the end (or to a surface it cannot
-// reach), then its outputs.
-template <int MODE>
-__device__ __forceinline__ void finish_one(const FitArgs& a, int64_t t, int l0, State<float>& s,
-                                           unsigned& st, unsigned& iters, bool alive) {
-  unsigned st1[1] = {st}, it1[1] = {iters};
-  if (alive) {
-    const int l = run_layers<MODE, float>(a, t, l0, s, st1, it1, alive);
-    if (l < a.nlayer) {
-      st1[0] |= FIT_ST_NO_INTERSECTION;
-      if (a.chi2_layer)
-        for (int r = l; r < a.nlayer; ++r) a.chi2_layer[(int64_t)r * a.ld_out + t] = 0.f;
-    }
-  }
-  store_state(a, t, s, st1);
-  st = st1[0];
-  iters = it1[0];
-}
-
-// Tracks t and t+1 of the launch's range [t0, t1) (t even).  Both valid: the
-// pair shares packed instructions until a surface that one of them cannot
-// reach, from where each finishes alone.  One valid (the range starts or ends
-// at an odd index): that one alone.
-template <int MODE>
-__device__ __forceinline__ void run_pair(const FitArgs& a, int64_t t, unsigned (&st)[2],
-                                         unsigned (&iters)[2]) {
-  const bool v0 = t >= a.t0, v1 = t + 1 < a.t1;
-  if (v0 && v1) {
-    State<F2> s;
-    load_state(a, t, s);
-    fitk::M2 alive = {true, true};
-    const int l = run_layers<MODE, F2>(a, t, 0, s, st, iters, alive);
-    if (l == a.nlayer) {
-      store_state(a, t, s, st);
-      return;
-    }
-#pragma unroll 1
-    for (int i = 0; i < 2; ++i) {
-      State<float> one = lane_of(s, i);
-      finish_one<MODE>(a, t + i, l, one, st[i], iters[i], Lanes<F2>::get(alive, i));
-    }
-  } else {
-    const int i = v0 ? 0 : 1;
-    State<float> one;
-    load_state(a, t + i, one);
-    finish_one<MODE>(a, t + i, 0, one, st[i], iters[i], true);
-  }
-}
-
-// First track of the thread's pair: pairs start at even indices so that the
-// packed loads and stores are 8-byte aligned.
-__device__ __forceinline__ int64_t pair_track(const FitArgs& a) {
-  return (a.t0 & ~int64_t(1)) + 2 * ((int64_t)blockIdx.x * kBlock + threadIdx.x);
-}
-
-__device__ __forceinline__ void count_iterations(unsigned iters, unsigned long long* counter) {
-  const unsigned mask = __activemask();
-  const unsigned warp_iters = __reduce_add_sync(mask, iters);
-  if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(counter, (unsigned long long)warp_iters);
-}
+namespace {
 
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) fit_fused_kernel(const __grid_constant__ FitArgs a) {
   const int64_t t = pair_track(a);
   if (t >= a.t1) return;
   unsigned st[2] = {0u, 0u}, iters[2] = {0u, 0u};
-  run_pair<MODE>(a, t, st, iters);
+  run_pair<MODE>(a, a.geo, a.t0, a.t1, t, st, iters);
   if (st[0]) count_status(st[0], a.counters);
   if (st[1]) count_status(st[1], a.counters);
   if (MODE == FIT_MODE_R) count_iterations(iters[0] + iters[1], &a.counters[4]);
-}
-
-// Variant for fit_propagate_update_noalloc: the same per-track work, with the
-// counters kept per event.  a.counters points at a [nevt][kEventSlots] table
-// (slot 0, the track count, is filled on the host); evt_off holds the first
-// track of events e0..e1 (and the end of e1 - 1), so a track finds its event
-// by binary search.
-constexpr int kEventSlots = 6;
-
-__device__ __forceinline__ int event_of(int64_t t, const int64_t* __restrict__ evt_off, int e0,
-                                        int e1) {
-  int lo = e0, hi = e1 - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (evt_off[mid] <= t)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
 }
 
 template <int MODE>
@@ -296,7 +47,7 @@ __global__ void __launch_bounds__(kBlock)
   const int64_t t = pair_track(a);
   if (t >= a.t1) return;
   unsigned st[2] = {0u, 0u}, iters[2] = {0u, 0u};
-  run_pair<MODE>(a, t, st, iters);
+  run_pair<MODE>(a, a.geo, a.t0, a.t1, t, st, iters);
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     if (t + i < a.t0 || t + i >= a.t1) continue;
@@ -306,35 +57,8 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
-bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
-class DeviceGuard {
- public:
-  explicit DeviceGuard(int dev) {
-    cudaGetDevice(&prev_);
-    if (prev_ != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() { cudaSetDevice(prev_); }
-
- private:
-  int prev_ = 0;
-};
 
 }  // namespace
-
-struct fit_handle {
-  int device = 0;
-  bool has[2] = {false, false};
-  int nlayer[2] = {0, 0};
-  float kB[2] = {0.f, 0.f};
-  int max_iter[2] = {10, 10};
-  float tol[2] = {1e-6f, 1e-6f};
-  Surfaces surf[2];
-  unsigned long long* d_counters = nullptr;  // [kCounters]
-  uint64_t tracks = 0;
-};
-
-namespace {
 
 // Copies the two modes' geometry and numerics into h (no allocation).
 int configure_modes(fit_handle* h, const fit_config* cfg_r, const fit_config* cfg_z,
@@ -348,13 +72,13 @@ int configure_modes(fit_handle* h, const fit_config* cfg_r, const fit_config* cf
     for (int l = 0; l < c->nlayer; ++l) {
       if (!(c->surf[l] == c->surf[l]) || (m == FIT_MODE_R && !(c->surf[l] > 0.f)))
         return fail(FIT_ERR_ARG, std::string(who) + ": invalid surface position");
-      h->surf[m].s[l] = c->surf[l];
+      h->geo[m].surf.s[l] = c->surf[l];
     }
     h->has[m] = true;
     h->nlayer[m] = c->nlayer;
-    h->kB[m] = fitk::kA * c->B;
-    h->max_iter[m] = c->max_iter > 0 ? c->max_iter : 10;
-    h->tol[m] = c->tol > 0.f ? c->tol : 1e-6f;
+    h->geo[m].kB = fitk::kA * c->B;
+    h->geo[m].max_iter = c->max_iter > 0 ? c->max_iter : 10;
+    h->geo[m].tol = c->tol > 0.f ? c->tol : 1e-6f;
   }
   return FIT_OK;
 }
@@ -430,10 +154,7 @@ int launch_segments(const fit_handle* h, FitArgs a, int nevt, const int64_t* ntr
     if (t1 > t) {
       a.t0 = t;
       a.t1 = t1;
-      a.kB = h->kB[m];
-      a.max_iter = h->max_iter[m];
-      a.tol = h->tol[m];
-      a.surf = h->surf[m];
+      a.geo = h->geo[m];
       const int64_t npairs = (t1 - (t & ~int64_t(1)) + 1) / 2;  // two tracks per thread
       const int64_t nblk = (npairs + kBlock - 1) / kBlock;
       if (nblk > 0x7fffffff) return fail(FIT_ERR_ARG, std::string(who) + ": too many tracks");
@@ -475,7 +196,9 @@ int noalloc_scratch(int device, unsigned long long** ptr) {
   return FIT_OK;
 }
 
-}  // namespace
+}  // namespace fitimpl
+
+using namespace fitimpl;
 
 extern "C" {
 

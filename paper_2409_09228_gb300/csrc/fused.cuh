@@ -1,0 +1,234 @@
+// Device side of the fused propagate + update fit: the per-track layer loop
+// over one or two tracks per thread, shared by the kernels of fit.cu and
+// batch.cu.
+//
+// One thread owns one or two tracks for all layers (paper Sec. 3.1:
+// propagation and update in one kernel; Sec. 4.2: per-track intermediates
+// kept in registers).  Track state and covariance are loaded once, stay in
+// registers through every layer, and are stored once.  Consecutive threads
+// read consecutive words of each hit component (structure of arrays, track
+// index fastest).
+#pragma once
+
+#include "internal.h"
+#include "track_math.cuh"
+
+namespace fitimpl {
+
+__device__ __forceinline__ void count_status(unsigned st, unsigned long long* counters) {
+  if (st & FIT_ST_NO_INTERSECTION) atomicAdd(&counters[0], 1ull);
+  if (st & FIT_ST_NOT_CONVERGED) atomicAdd(&counters[1], 1ull);
+  if (st & FIT_ST_NONFINITE) atomicAdd(&counters[2], 1ull);
+  if (st & FIT_ST_CHARGE_FLIP) atomicAdd(&counters[3], 1ull);
+}
+
+using fitk::F2;
+using fitk::Lanes;
+
+// One or two tracks (lane type T) in registers for the whole layer loop.
+template <class T>
+struct State {
+  T p[6], c[21];
+  T qf;    // charge as +-1.f
+  T chi2;  // sum over layers
+  fitk::Trig<T> g;
+};
+
+template <class T>
+__device__ __forceinline__ void load_state(const FitArgs& a, int64_t t, State<T>& s);
+template <>
+__device__ __forceinline__ void load_state(const FitArgs& a, int64_t t, State<float>& s) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) fitk::ld(s.p[k], a.par_in + k * a.ld_in + t);
+#pragma unroll
+  for (int k = 0; k < 21; ++k) fitk::ld(s.c[k], a.cov_in + k * a.ld_in + t);
+  s.qf = (float)__ldcs(a.q_in + t);
+  s.chi2 = 0.f;
+  s.g = fitk::trig_of(s.p);
+}
+template <>
+__device__ __forceinline__ void load_state(const FitArgs& a, int64_t t, State<F2>& s) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) fitk::ld(s.p[k], a.par_in + k * a.ld_in + t);
+#pragma unroll
+  for (int k = 0; k < 21; ++k) fitk::ld(s.c[k], a.cov_in + k * a.ld_in + t);
+  const int2 q = __ldcs(reinterpret_cast<const int2*>(a.q_in + t));
+  s.qf = F2((float)q.x, (float)q.y);
+  s.chi2 = F2(0.f);
+  s.g = fitk::trig_of(s.p);
+}
+
+// Lane i of a two-track state as a one-track state.
+__device__ __forceinline__ State<float> lane_of(const State<F2>& s, int i) {
+  State<float> r;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.p[k] = Lanes<F2>::get(s.p[k], i);
+#pragma unroll
+  for (int k = 0; k < 21; ++k) r.c[k] = Lanes<F2>::get(s.c[k], i);
+  r.qf = Lanes<F2>::get(s.qf, i);
+  r.chi2 = Lanes<F2>::get(s.chi2, i);
+  r.g = {Lanes<F2>::get(s.g.cphi, i), Lanes<F2>::get(s.g.sphi, i), Lanes<F2>::get(s.g.cth, i),
+         Lanes<F2>::get(s.g.sth, i)};
+  return r;
+}
+
+// Writes the outputs of the lanes of s (tracks t, t+1, ...), after the final
+// finiteness check.
+template <class T>
+__device__ __forceinline__ void store_state(const FitArgs& a, int64_t t, const State<T>& s,
+                                            unsigned (&st)[Lanes<T>::n]) {
+  auto fin = fitk::finite_(s.chi2);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) fin = fitk::and_(fin, fitk::finite_(s.p[k]));
+#pragma unroll
+  for (int k = 0; k < 21; ++k) fin = fitk::and_(fin, fitk::finite_(s.c[k]));
+#pragma unroll
+  for (int i = 0; i < Lanes<T>::n; ++i)
+    if (!Lanes<T>::get(fin, i)) st[i] |= FIT_ST_NONFINITE;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) fitk::st(a.par_out + k * a.ld_out + t, s.p[k]);
+#pragma unroll
+  for (int k = 0; k < 21; ++k) fitk::st(a.cov_out + k * a.ld_out + t, s.c[k]);
+  fitk::st(a.chi2 + t, s.chi2);
+#pragma unroll
+  for (int i = 0; i < Lanes<T>::n; ++i) {
+    a.q_out[t + i] = (int32_t)Lanes<T>::get(s.qf, i);
+    if (a.status) a.status[t + i] = (uint8_t)st[i];
+  }
+}
+
+// The fused layer loop (paper Sec. 3.1: propagate to the next layer, update
+// with its hit) for the lanes of s, tracks t, t+1, ..., from layer l0.
+// MODE selects the surface type at compile time.  Returns the layer whose
+// surface some live lane cannot reach (its propagation is not applied), or
+// nlayer.  A lane whose update turns non-finite stops (alive false); its
+// later per-layer chi2 entries are 0.
+template <int MODE, class T>
+__device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int64_t t, int l0,
+                                          State<T>& s,
+                                          unsigned (&st)[Lanes<T>::n],
+                                          unsigned (&iters)[Lanes<T>::n],
+                                          typename Lanes<T>::M& alive) {
+  using M = typename Lanes<T>::M;
+  const float* hp = a.hpos + t;
+  const float* hc = a.hcov + t;
+  const int64_t ldh = a.ld_hit;
+  for (int l = l0; l < a.nlayer; ++l) {
+    T m[3], v[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fitk::ld(m[k], hp + (3 * l + k) * ldh);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) fitk::ld(v[k], hc + (6 * l + k) * ldh);
+    const float sf = geo.surf.s[l];
+    const T dkdw = s.qf * T(-geo.kB);
+    M fail, nc = fitk::lt(T(1.f), T(0.f));
+    if (MODE == FIT_MODE_Z)
+      fail = fitk::prop_z(s.p, s.c, s.g, dkdw, sf);
+    else
+      fail = fitk::prop_r(s.p, s.c, s.g, dkdw, sf, geo.max_iter, geo.tol * sf, iters, nc);
+    if (fitk::any(fitk::and_(fail, alive))) return l;
+    const T phi_pred = s.p[4], th_pred = s.p[5];
+    T x2 = (MODE == FIT_MODE_Z) ? fitk::update_z(s.p, s.c, m, v) : fitk::update_r(s.p, s.c, m, v);
+    const M flip = fitk::normalise(s.p, s.c, s.qf, s.g, phi_pred, th_pred);
+    alive = fitk::and_(alive, fitk::finite_(x2));
+#pragma unroll
+    for (int i = 0; i < Lanes<T>::n; ++i) {
+      if (Lanes<T>::get(nc, i)) st[i] |= FIT_ST_NOT_CONVERGED;
+      if (Lanes<T>::get(flip, i)) st[i] |= FIT_ST_CHARGE_FLIP;
+      if (!Lanes<T>::get(alive, i)) st[i] |= FIT_ST_NONFINITE;
+    }
+    x2 = fitk::sel(alive, x2, T(0.f));
+    s.chi2 += x2;
+    if (a.chi2_layer) fitk::st(a.chi2_layer + (int64_t)l * a.ld_out + t, x2);
+    if (!fitk::any(alive)) {
+      if (a.chi2_layer)
+        for (int r = l + 1; r < a.nlayer; ++r) fitk::st(a.chi2_layer + (int64_t)r * a.ld_out + t, T(0.f));
+      return a.nlayer;
+    }
+  }
+  return a.nlayer;
+}
+
+// One track alone from layer l0 to the end (or to a surface it cannot
+// reach), then its outputs.
+template <int MODE>
+__device__ __forceinline__ void finish_one(const FitArgs& a, const Geo& geo, int64_t t, int l0,
+                                           State<float>& s, unsigned& st, unsigned& iters,
+                                           bool alive) {
+  unsigned st1[1] = {st}, it1[1] = {iters};
+  if (alive) {
+    const int l = run_layers<MODE, float>(a, geo, t, l0, s, st1, it1, alive);
+    if (l < a.nlayer) {
+      st1[0] |= FIT_ST_NO_INTERSECTION;
+      if (a.chi2_layer)
+        for (int r = l; r < a.nlayer; ++r) a.chi2_layer[(int64_t)r * a.ld_out + t] = 0.f;
+    }
+  }
+  store_state(a, t, s, st1);
+  st = st1[0];
+  iters = it1[0];
+}
+
+// Tracks t and t+1 of the range [t0, t1) (t even).  Both valid: the pair
+// shares packed instructions until a surface that one of them cannot reach,
+// from where each finishes alone.  One valid (the range starts or ends at an
+// odd index): that one alone.
+template <int MODE>
+__device__ __forceinline__ void run_pair(const FitArgs& a, const Geo& geo, int64_t t0, int64_t t1,
+                                         int64_t t, unsigned (&st)[2], unsigned (&iters)[2]) {
+  const bool v0 = t >= t0, v1 = t + 1 < t1;
+  if (v0 && v1) {
+    State<F2> s;
+    load_state(a, t, s);
+    fitk::M2 alive = {true, true};
+    const int l = run_layers<MODE, F2>(a, geo, t, 0, s, st, iters, alive);
+    if (l == a.nlayer) {
+      store_state(a, t, s, st);
+      return;
+    }
+#pragma unroll 1
+    for (int i = 0; i < 2; ++i) {
+      State<float> one = lane_of(s, i);
+      finish_one<MODE>(a, geo, t + i, l, one, st[i], iters[i], Lanes<F2>::get(alive, i));
+    }
+  } else {
+    const int i = v0 ? 0 : 1;
+    State<float> one;
+    load_state(a, t + i, one);
+    finish_one<MODE>(a, geo, t + i, 0, one, st[i], iters[i], true);
+  }
+}
+
+// First track of the thread's pair: pairs start at even indices so that the
+// packed loads and stores are 8-byte aligned.
+__device__ __forceinline__ int64_t pair_track(const FitArgs& a) {
+  return (a.t0 & ~int64_t(1)) + 2 * ((int64_t)blockIdx.x * kBlock + threadIdx.x);
+}
+
+__device__ __forceinline__ void count_iterations(unsigned iters, unsigned long long* counter) {
+  const unsigned mask = __activemask();
+  const unsigned warp_iters = __reduce_add_sync(mask, iters);
+  if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(counter, (unsigned long long)warp_iters);
+}
+
+// Variant for fit_propagate_update_noalloc: the same per-track work, with the
+// counters kept per event.  a.counters points at a [nevt][kEventSlots] table
+// (slot 0, the track count, is filled on the host); evt_off holds the first
+// track of events e0..e1 (and the end of e1 - 1), so a track finds its event
+// by binary search.
+constexpr int kEventSlots = 6;
+
+__device__ __forceinline__ int event_of(int64_t t, const int64_t* __restrict__ evt_off, int e0,
+                                        int e1) {
+  int lo = e0, hi = e1 - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (evt_off[mid] <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace fitimpl

@@ -1,0 +1,93 @@
+// Internal declarations shared by the libfit translation units (not part of
+// the C ABI).  Host-side helpers and the kernel argument blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "fit.h"
+
+namespace fitimpl {
+
+// Error reporting: the message of the last failure on the calling thread.
+extern thread_local std::string g_last_error;
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+constexpr int kBlock = 128;
+constexpr int kCounters = 5;  // no_intersection, not_converged, nonfinite, charge_flip,
+                               // p2r path-length iterations
+
+struct Surfaces {
+  float s[FIT_MAX_LAYERS];
+};
+
+// Geometry and numerics of one mode.
+struct Geo {
+  float kB;  // kA * B
+  int max_iter;
+  float tol;
+  Surfaces surf;
+};
+
+struct FitArgs {
+  const float* par_in;
+  const float* cov_in;
+  const int32_t* q_in;
+  int64_t ld_in;
+  float* par_out;
+  float* cov_out;
+  int32_t* q_out;
+  float* chi2;
+  float* chi2_layer;
+  uint8_t* status;
+  int64_t ld_out;
+  const float* hpos;
+  const float* hcov;
+  int64_t ld_hit;
+  int64_t t0, t1;  // track range [t0, t1)
+  int nlayer;
+  unsigned long long* counters;
+  Geo geo;
+};
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() { cudaSetDevice(prev_); }
+
+ private:
+  int prev_ = 0;
+};
+
+
+}  // namespace fitimpl
+
+
+struct fit_handle {
+  int device = 0;
+  bool has[2] = {false, false};
+  int nlayer[2] = {0, 0};
+  fitimpl::Geo geo[2];
+  unsigned long long* d_counters = nullptr;  // [kCounters]
+  uint64_t tracks = 0;
+};
+
+
+namespace fitimpl {
+
+// Argument checks shared by the entry points that run the fused kernel.
+int check_call(const fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
+               const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
+               const int32_t* mode, int64_t* total_out, const char* who);
+FitArgs base_args(const fit_tracks_in* in, const fit_tracks_out* out, const fit_hits* hits,
+                  int nlayer, unsigned long long* counters);
+
+}  // namespace fitimpl

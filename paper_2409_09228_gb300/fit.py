@@ -67,8 +67,19 @@ class fit_status(ctypes.Structure):
                 ("charge_flip", ctypes.c_uint64), ("iterations", ctypes.c_uint64)]
 
 
+class fit_launch_config(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("persistent", ctypes.c_int)]
+
+
+class fit_plan_info(ctypes.Structure):
+    _fields_ = [("config", fit_launch_config), ("tracks", ctypes.c_int64),
+                ("items", ctypes.c_int32), ("tuned", ctypes.c_int32), ("best_ms", ctypes.c_float)]
+
+
 EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_last_error",
-           "fit_propagate_update_noalloc")
+           "fit_propagate_update_noalloc", "fit_plan_create", "fit_plan_run", "fit_plan_tune",
+           "fit_plan_get_info", "fit_plan_destroy")
 FIT_NOALLOC_MAX_EVENTS = 4096
 
 _lib = None
@@ -110,6 +121,20 @@ def load(build_if_missing: bool = True):
         ctypes.POINTER(i64), ctypes.c_int, ctypes.POINTER(ctypes.c_int32), vp,
         ctypes.POINTER(fit_status)]
     L.fit_propagate_update_noalloc.restype = ctypes.c_int
+    L.fit_plan_create.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64),
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                  ctypes.POINTER(fit_launch_config), ctypes.POINTER(vp)]
+    L.fit_plan_create.restype = ctypes.c_int
+    L.fit_plan_run.argtypes = [vp, ctypes.POINTER(fit_tracks_in), ctypes.POINTER(fit_tracks_out),
+                               ctypes.POINTER(fit_hits), vp]
+    L.fit_plan_run.restype = ctypes.c_int
+    L.fit_plan_tune.argtypes = [vp, ctypes.POINTER(fit_tracks_in), ctypes.POINTER(fit_tracks_out),
+                                ctypes.POINTER(fit_hits), vp, ctypes.c_char_p]
+    L.fit_plan_tune.restype = ctypes.c_int
+    L.fit_plan_get_info.argtypes = [vp, ctypes.POINTER(fit_plan_info)]
+    L.fit_plan_get_info.restype = ctypes.c_int
+    L.fit_plan_destroy.argtypes = [vp]
+    L.fit_plan_destroy.restype = None
     _lib = L
     return L
 
@@ -209,6 +234,63 @@ def fit_propagate_update_noalloc(geom_r: Optional[Geometry], geom_z: Optional[Ge
     if not per_event:
         return None
     return [{k: int(getattr(st[e], k)) for k, _ in fit_status._fields_} for e in range(len(nt))]
+
+
+def _buffers(par_in, cov_in, q_in, hpos, hcov, par_out, cov_out, q_out, chi2, chi2_layer, status):
+    par_out = par_in if par_out is None else par_out
+    cov_out = cov_in if cov_out is None else cov_out
+    q_out = q_in if q_out is None else q_out
+    tin = fit_tracks_in(_ptr(par_in), _ptr(cov_in), _ptr(q_in), par_in.shape[-1])
+    tout = fit_tracks_out(_ptr(par_out), _ptr(cov_out), _ptr(q_out), _ptr(chi2),
+                          _ptr(chi2_layer), _ptr(status), par_out.shape[-1])
+    return tin, tout, fit_hits(_ptr(hpos), _ptr(hcov), hpos.shape[-1])
+
+
+def fit_plan_create(h: int, ntrk: Sequence[int], mode: Sequence[int], nlayer: int,
+                    threads_per_block: int = 128, blocks_per_sm: int = 0,
+                    persistent: bool = True) -> int:
+    """A plan for the batched persistent form (see fit.h)."""
+    nt = np.ascontiguousarray(ntrk, dtype=np.int64)
+    md = np.ascontiguousarray(mode, dtype=np.int32)
+    cfg = fit_launch_config(threads_per_block, blocks_per_sm, int(persistent))
+    p = ctypes.c_void_p()
+    _check(load().fit_plan_create(ctypes.c_void_p(h), len(nt),
+                                  nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), nlayer,
+                                  ctypes.byref(cfg), ctypes.byref(p)))
+    return p.value
+
+
+def fit_plan_run(plan: int, par_in, cov_in, q_in, hpos, hcov, par_out=None, cov_out=None,
+                 q_out=None, chi2=None, chi2_layer=None, status=None, stream=None) -> None:
+    tin, tout, hits = _buffers(par_in, cov_in, q_in, hpos, hcov, par_out, cov_out, q_out, chi2,
+                               chi2_layer, status)
+    _check(load().fit_plan_run(ctypes.c_void_p(plan), ctypes.byref(tin), ctypes.byref(tout),
+                               ctypes.byref(hits), _stream_handle(stream)))
+
+
+def fit_plan_tune(plan: int, par_in, cov_in, q_in, hpos, hcov, par_out, cov_out, q_out, chi2,
+                  chi2_layer=None, status=None, stream=None, cache_path: Optional[str] = None) -> dict:
+    tin, tout, hits = _buffers(par_in, cov_in, q_in, hpos, hcov, par_out, cov_out, q_out, chi2,
+                               chi2_layer, status)
+    _check(load().fit_plan_tune(ctypes.c_void_p(plan), ctypes.byref(tin), ctypes.byref(tout),
+                                ctypes.byref(hits), _stream_handle(stream),
+                                cache_path.encode() if cache_path else None))
+    return fit_plan_get_info(plan)
+
+
+def fit_plan_get_info(plan: int) -> dict:
+    info = fit_plan_info()
+    _check(load().fit_plan_get_info(ctypes.c_void_p(plan), ctypes.byref(info)))
+    c = info.config
+    return {"threads_per_block": c.threads_per_block, "blocks_per_sm": c.blocks_per_sm,
+            "persistent": bool(c.persistent), "tracks": info.tracks, "items": info.items,
+            "tuned": info.tuned, "best_ms": info.best_ms}
+
+
+def fit_plan_destroy(plan: int) -> None:
+    if plan:
+        load().fit_plan_destroy(ctypes.c_void_p(plan))
 
 
 def fit_sync(h: int, stream=None, timeout_s: float = 0.0) -> dict:

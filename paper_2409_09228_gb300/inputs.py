@@ -191,3 +191,52 @@ def uneven_event_sizes(nevt: int, seed: int, median: float = 2000.0, sigma_ln: f
 def uneven_event_modes(nevt: int, seed: int) -> np.ndarray:
     """Mode per event, p2r or p2z with probability 1/2."""
     return np.where(_rng(seed, 17).random(nevt) < 0.5, MODE_R, MODE_Z).astype(np.int32)
+
+
+@dataclass
+class EventSet:
+    """Events stored one after another (event e holds ntrk[e] tracks of mode[e])."""
+    ntrk: np.ndarray          # (nevt,) int64
+    mode: np.ndarray          # (nevt,) int32
+    B: float
+    surf: tuple               # (p2r radii, p2z z positions), float32
+    par0: np.ndarray          # (6, n)
+    cov0: np.ndarray          # (21, n)
+    q: np.ndarray             # (n,)
+    hpos: np.ndarray          # (nlayer, 3, n)
+    hcov: np.ndarray          # (nlayer, 6, n)
+
+    @property
+    def n(self) -> int:
+        return int(self.ntrk.sum())
+
+    def starts(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.ntrk)]).astype(np.int64)
+
+    def event(self, e: int) -> TrackSet:
+        s = self.starts()
+        a, b = int(s[e]), int(s[e + 1])
+        m = int(self.mode[e])
+        return TrackSet(m, self.B, self.surf[m], self.par0[:, a:b], self.cov0[:, a:b],
+                        self.q[a:b], self.hpos[:, :, a:b], self.hcov[:, :, a:b])
+
+
+def generate_events(ntrk, modes, seed: int, nlayer: int = NLAYER, B: float = B_FIELD) -> EventSet:
+    """Events of the given sizes and modes; the tracks of each mode come from
+    one generate() call (seed, seed + 1), dealt out to that mode's events in
+    order."""
+    ntrk = np.asarray(ntrk, np.int64)
+    modes = np.asarray(modes, np.int32)
+    pools = [generate(m, int(ntrk[modes == m].sum()), seed=seed + m, nlayer=nlayer, B=B)
+             for m in (MODE_R, MODE_Z)]
+    # position in the concatenation [pool r | pool z] of every track, in event order
+    next_idx = [0, pools[0].n]
+    idx = np.empty(int(ntrk.sum()), np.int64)
+    pos = 0
+    for k, m in zip(ntrk, modes):
+        idx[pos:pos + k] = np.arange(next_idx[m], next_idx[m] + k)
+        next_idx[m] += k
+        pos += k
+    cat = lambda name: np.concatenate([getattr(pools[0], name), getattr(pools[1], name)], axis=-1)[..., idx]  # noqa: E731
+    return EventSet(ntrk, modes, pools[0].B, (pools[0].surf, pools[1].surf), cat("par0"),
+                    cat("cov0"), cat("q"), cat("hpos"), cat("hcov"))

@@ -64,3 +64,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(fit.fit_tracks_out) == 56
     assert ctypes.sizeof(fit.fit_hits) == 24
     assert ctypes.sizeof(fit.fit_status) == 48
+
+
+def test_plan_struct_layouts():
+    assert ctypes.sizeof(fit.fit_launch_config) == 12
+    assert ctypes.sizeof(fit.fit_plan_info) == 40

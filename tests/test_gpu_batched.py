@@ -1,0 +1,158 @@
+"""The batched persistent form (fit_plan_*): uneven events of both modes in one
+launch under a CUDA graph, against the FP64 oracle and against the per-segment
+path; every launch shape the autotuner can pick; the tuning cache."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import parity
+from paper_2409_09228_gb300 import fit, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import gpu_util  # noqa: E402
+
+
+def _events(nevt=60, seed=31):
+    """Log-normal event sizes (median 60, clipped 1..400), a few empty events,
+    modes p2r/p2z at random."""
+    nt = inputs.uneven_event_sizes(nevt, seed, median=60.0, lo=1, hi=400)
+    nt[[i for i in (3, 17) if i < nevt]] = 0
+    md = inputs.uneven_event_modes(nevt, seed)
+    return inputs.generate_events(nt, md, seed=seed)
+
+
+def _device(ev, ld=None):
+    ld = ld or gpu_util.pad_ld(ev.n)
+    return ld, [gpu_util.to_dev(a, ld) for a in (ev.par0, ev.cov0, ev.q, ev.hpos, ev.hcov)]
+
+
+def _geoms(ev):
+    return fit.Geometry(ev.B, ev.surf[0]), fit.Geometry(ev.B, ev.surf[1])
+
+
+def _outputs(f, ev, ld):
+    out = f.outputs(ev.n, ld=ld)
+    for k in ("par", "cov", "chi2"):
+        out[k].fill_(float("nan"))
+    return out
+
+
+def _fetch(out, n):
+    return {k: v.cpu().numpy()[..., :n] for k, v in out.items() if v is not None}
+
+
+def _check_against_oracle(ev, got, label):
+    s = ev.starts()
+    for e in range(len(ev.ntrk)):
+        if ev.ntrk[e] == 0:
+            continue
+        sub = {k: v[..., s[e]:s[e + 1]] for k, v in got.items()}
+        parity.check(sub, oracle.fit_set(ev.event(e)), f"{label} event {e}")
+
+
+def test_plan_matches_oracle_and_segments():
+    ev = _events()
+    ld, dev_in = _device(ev)
+    f = fit.Fitter(*_geoms(ev))
+    plan = fit.fit_plan_create(f.h, ev.ntrk, ev.mode, 20)
+    try:
+        info = fit.fit_plan_get_info(plan)
+        assert info["persistent"] and info["tracks"] == ev.n and info["items"] > 0
+        out = _outputs(f, ev, ld)
+        fit.fit_plan_run(plan, *dev_in, par_out=out["par"], cov_out=out["cov"], q_out=out["q"],
+                         chi2=out["chi2"], status=out["status"])
+        st = f.sync()
+        assert st["tracks"] == ev.n and st["nonfinite"] == 0 and st["no_intersection"] == 0
+        got = _fetch(out, ev.n)
+        _check_against_oracle(ev, got, "plan")
+        # the per-segment path on the same events agrees within the tolerance
+        seg = _fetch(f.run(*dev_in, ev.ntrk, ev.mode), ev.n)
+        f.sync()
+        parity.check(got, seg, "plan vs segments")
+        # a second run replays the graph; a new output set is captured anew
+        out2 = _outputs(f, ev, ld)
+        for _ in range(2):
+            fit.fit_plan_run(plan, *dev_in, par_out=out2["par"], cov_out=out2["cov"],
+                             q_out=out2["q"], chi2=out2["chi2"], status=out2["status"])
+        f.sync()
+        got2 = _fetch(out2, ev.n)
+        for k in ("par", "cov", "q", "chi2", "status"):
+            assert np.array_equal(got2[k], got[k]), k
+    finally:
+        fit.fit_plan_destroy(plan)
+        f.close()
+
+
+@pytest.mark.parametrize("tpb,bps,persistent", [(64, 1, 1), (64, 6, 1), (128, 1, 1), (128, 3, 1),
+                                                (128, 0, 0)])
+def test_every_launch_shape(tpb, bps, persistent):
+    ev = _events(40, seed=41)
+    ld, dev_in = _device(ev)
+    f = fit.Fitter(*_geoms(ev))
+    plan = fit.fit_plan_create(f.h, ev.ntrk, ev.mode, 20, threads_per_block=tpb,
+                               blocks_per_sm=bps, persistent=bool(persistent))
+    try:
+        out = _outputs(f, ev, ld)
+        fit.fit_plan_run(plan, *dev_in, par_out=out["par"], cov_out=out["cov"], q_out=out["q"],
+                         chi2=out["chi2"], status=out["status"])
+        f.sync()
+        _check_against_oracle(ev, _fetch(out, ev.n), f"shape {tpb},{bps},{persistent}")
+    finally:
+        fit.fit_plan_destroy(plan)
+        f.close()
+
+
+def test_tune_and_cache(tmp_path):
+    ev = _events(80, seed=51)
+    ld, dev_in = _device(ev)
+    f = fit.Fitter(*_geoms(ev))
+    cache = str(tmp_path / "tune.txt")
+    out = _outputs(f, ev, ld)
+    bufs = dict(par_out=out["par"], cov_out=out["cov"], q_out=out["q"], chi2=out["chi2"],
+                status=out["status"])
+    p1 = fit.fit_plan_create(f.h, ev.ntrk, ev.mode, 20)
+    p2 = fit.fit_plan_create(f.h, ev.ntrk, ev.mode, 20)
+    try:
+        f.sync()
+        info = fit.fit_plan_tune(p1, *dev_in, cache_path=cache, **bufs)
+        assert info["tuned"] == 1 and info["best_ms"] > 0
+        assert os.path.exists(cache) and open(cache).read().count("\t") == 1
+        assert f.sync()["tracks"] == 0  # the tuning runs are not counted
+        info2 = fit.fit_plan_tune(p2, *dev_in, cache_path=cache, **bufs)
+        assert info2["tuned"] == 2
+        for k in ("threads_per_block", "blocks_per_sm", "persistent"):
+            assert info2[k] == info[k]
+        fit.fit_plan_run(p2, *dev_in, **bufs)
+        f.sync()
+        _check_against_oracle(ev, _fetch(out, ev.n), "tuned plan")
+        # tuning must not overwrite its own inputs
+        with pytest.raises(fit.FitError) as e:
+            fit.fit_plan_tune(p1, *dev_in, par_out=dev_in[0], cov_out=dev_in[1], q_out=dev_in[2],
+                              chi2=out["chi2"])
+        assert e.value.code == fit.FIT_ERR_ARG
+    finally:
+        fit.fit_plan_destroy(p1)
+        fit.fit_plan_destroy(p2)
+        f.close()
+
+
+def test_plan_argument_errors():
+    ev = _events(10, seed=61)
+    f = fit.Fitter(fit.Geometry(ev.B, ev.surf[0]), None)  # p2z not configured
+    try:
+        with pytest.raises(fit.FitError) as e:
+            fit.fit_plan_create(f.h, ev.ntrk, ev.mode, 20)
+        assert e.value.code == fit.FIT_ERR_ARG
+        with pytest.raises(fit.FitError):
+            fit.fit_plan_create(f.h, [10], [0], 19)  # nlayer differs
+        with pytest.raises(fit.FitError):
+            fit.fit_plan_create(f.h, [10], [0], 20, threads_per_block=96)
+    finally:
+        f.close()
