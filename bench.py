@@ -293,6 +293,71 @@ def bench_uneven(args, world, rank, local):
     print(json.dumps(line))
 
 
+def bench_adjoint(args, world, rank, local):
+    """Gradient of the summed chi2 w.r.t. hit positions and initial parameters
+    for 100k p2r tracks x 20 layers (forward with per-layer checkpoints, then
+    the reverse sweep), against the FP64 oracle's dual-number gradient timed on
+    the host cores over a sample."""
+    import torch
+    from paper_2409_09228_gb300 import fit, inputs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n = args.adjoint_tracks
+    ts = inputs.generate(inputs.MODE_R, n, seed=5 + 1000 * rank)
+    ld = (n + 3) // 4 * 4
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(np.pad(a, [(0, 0)] * (a.ndim - 1) + [(0, ld - n)]))).to(dev)  # noqa: E731
+    d = [up(a) for a in (ts.par0, ts.cov0, ts.q, ts.hpos, ts.hcov)]
+    f = fit.Fitter(fit.Geometry(ts.B, ts.surf), None, device=local)
+    tape = torch.empty(fit.fit_tape_bytes(NLAYER, ld) // 4, device=dev)
+    out = f.outputs(n, ld=ld)
+    w = torch.ones(ld, device=dev)
+    gh = torch.empty_like(d[3])
+    gp = torch.empty((6, ld), device=dev)
+    gc = torch.empty((21, ld), device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        fit.fit_adjoint_forward(f.h, *d, [n], [0], tape, out["par"], out["cov"], out["q"],
+                                out["chi2"], stream=stream)
+        fit.fit_adjoint_backward(f.h, d[3], d[4], [n], [0], tape, w, gh, gp, gc, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
+    f.sync(stream)
+    f.close()
+    if rank != 0:
+        return
+    line = {"metric": "track-layer chi2-gradient/s", "value": world * n * NLAYER / (ms / 1e3),
+            "unit": "track-layer/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"adjoint: d(sum chi2)/d(hit positions, initial parameters), "
+                                   f"{n} p2r tracks x {NLAYER} layers, per-layer checkpoints",
+                       "tape_bytes": fit.fit_tape_bytes(NLAYER, ld)}}
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cores = len(os.sched_getaffinity(0))
+        m = 2000
+        sub = ts.subset(np.arange(m))
+        t0 = time.perf_counter()
+        oracle.chi2_grad(sub.mode, sub.B, sub.surf, sub.par0, sub.cov0, sub.q, sub.hpos, sub.hcov,
+                         nthreads=cores)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": m * NLAYER / dt, "unit": "track-layer/s", "cores": cores,
+                                "kind": "oracle", "sample": f"{m} of {n} tracks, FP64 dual numbers, {dt:.1f} s"}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -302,10 +367,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--nevt", type=int, default=NEVT, help="events per mode (default 100)")
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven"],
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven", "adjoint"],
                     help="uniform: 100 x 9600 x 20 per mode (the default); uneven: the batched "
                          "form on 2000 events of log-normal size and mixed modes")
     ap.add_argument("--uneven-events", type=int, default=2000)
+    ap.add_argument("--adjoint-tracks", type=int, default=100000)
     args = ap.parse_args()
     set_nevt(args.nevt)
     args.warmup = max(args.warmup, 3)
@@ -315,6 +381,9 @@ def main():
         return
     if args.workload == "uneven":
         bench_uneven(args, world, rank, local)
+        return
+    if args.workload == "adjoint":
+        bench_adjoint(args, world, rank, local)
         return
 
     import torch

@@ -246,6 +246,39 @@ int fit_plan_get_info(const fit_plan* plan, fit_plan_info* info);
 /* fit_plan_destroy: frees the plan (after its pending work ends). */
 void fit_plan_destroy(fit_plan* plan);
 
+/*
+ * Gradient of each track's summed chi2 with respect to its hit positions and
+ * its initial parameters (and covariance): a reverse sweep over the layers,
+ * written by hand, from per-layer checkpoints.
+ *
+ * fit_tape_bytes: size of the tape for nlayer layers and leading dimension ld
+ * (per track and layer the state at the layer's entry -- 6 parameters, 21
+ * covariance entries, the charge before and after the update, as floats --
+ * then one int32 per track, the number of layers it completed).
+ *
+ * fit_adjoint_forward: as fit_propagate_update (same arguments and outputs;
+ * out->ld must equal hits->ld), one track per thread, and writes the tape
+ * (DEVICE, caller-owned, fit_tape_bytes(nlayer, out->ld) bytes, 16-byte
+ * aligned).  Counts into the handle like fit_propagate_update.
+ *
+ * fit_adjoint_backward: for every track t of the events, with weight
+ * grad_chi2[t] (the derivative of the caller's loss with respect to the
+ * track's summed chi2), writes
+ *   grad_hpos[(l*3 + k)*ld + t] = grad_chi2[t] * d chi2_t / d hit_pos[l][k]
+ *   grad_par0[k*ld + t]        = grad_chi2[t] * d chi2_t / d par_in[k]
+ *   grad_cov0[k*ld + t]        = grad_chi2[t] * d chi2_t / d cov_in[k]
+ *                                (packed entry k; grad_cov0 may be NULL)
+ * from the tape of a fit_adjoint_forward on the same inputs (ld = hits->ld).
+ * Layers a track did not complete contribute nothing.  All pointers DEVICE.
+ */
+size_t fit_tape_bytes(int nlayer, int64_t ld);
+int fit_adjoint_forward(fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
+                        const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
+                        const int32_t* mode, void* tape, void* stream);
+int fit_adjoint_backward(fit_handle* h, const fit_hits* hits, int nevt, const int64_t* ntrk,
+                         int nlayer, const int32_t* mode, const void* tape, const float* grad_chi2,
+                         float* grad_hpos, float* grad_par0, float* grad_cov0, void* stream);
+
 /* fit_destroy: frees the handle and its scratch (after pending work ends). */
 void fit_destroy(fit_handle* h);
 

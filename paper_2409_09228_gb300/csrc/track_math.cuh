@@ -265,20 +265,28 @@ __device__ __forceinline__ typename Lanes<T>::M prop_z(T (&p)[6], T (&c)[21], Tr
   return fail;
 }
 
-// Propagation to the cylinder r = R by straight-line steps along the current
-// direction.  Returns the mask of lanes that cannot reach the cylinder; if
-// any lane fails nothing is modified.  iters[i] counts lane i's iterations;
-// notconv marks lanes that reached max_iter.
+// Path length to the cylinder r = R by straight-line steps along the current
+// direction: the first step from (x, y) along phi, then repeatedly the helix
+// at h and a straight step along its direction to the circle, until a step is
+// below tol_abs.  Returns the mask of lanes that cannot reach the cylinder
+// (the other outputs are then meaningless).  On return h is the path length;
+// the helix quantities (u, s, cu, cm, sm, px, py, c1, s1) are those of the
+// last evaluation, at h - d.  iters[i] counts lane i's iterations; notconv
+// marks lanes that reached max_iter.
 template <class T>
-__device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Trig<T>& g, T dkdw,
+struct PathR {
+  T h, d, u, s, cu, cm, sm, px, py, c1, s1;
+};
+
+template <class T>
+__device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Trig<T>& g, T kappa,
                                                        float R, int max_iter, float tol_abs,
                                                        unsigned (&iters)[Lanes<T>::n],
-                                                       typename Lanes<T>::M& notconv) {
+                                                       typename Lanes<T>::M& notconv, PathR<T>& w) {
   using M = typename Lanes<T>::M;
   const T sph = g.sphi, cph = g.cphi;
   const T x = p[0], y = p[1];
   const T R2 = T(R * R);
-  const T kappa = dkdw * p[3];
   // The transverse circle (centre c, radius rho = 1/|kappa|) reaches radius
   // R only if |c| + rho >= R, which always holds when rho >= R.
   M fail = lt(T(1.f), T(R) * fabs_(kappa));
@@ -297,9 +305,8 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
   fail = or_(fail, or_(lt(disc0, T(0.f)), and_(not_(inside), not_(lt(b0, T(0.f))))));
   if (any(fail)) return fail;
   T h = sel(inside, sel(lt(T(0.f), b0), fdiv(-c0, b0 + sq0), sq0 - b0), fdiv(c0, sq0 - b0));
-  // Iterate: helix at h, then a straight step along its direction to the
-  // circle.  The directions phi + u and phi + 2u come from turning
-  // (cos phi, sin phi) by u.  A lane that has converged keeps its h.
+  // The directions phi + u and phi + 2u come from turning (cos phi, sin phi)
+  // by u.  A lane that has converged keeps its h.
   M conv = lt(T(1.f), T(0.f));  // all false
   T u = T(0.f), s = T(1.f), cu = T(1.f), sm = sph, cm = cph, px = x, py = y, c1 = cph, s1 = sph,
     d = T(0.f);
@@ -329,6 +336,25 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
     if (all(conv)) break;
   }
   notconv = not_(conv);
+  w = {h, d, u, s, cu, cm, sm, px, py, c1, s1};
+  return fail;
+}
+
+// Propagation to the cylinder r = R (path length from path_r).  Returns the
+// mask of lanes that cannot reach the cylinder; if any lane fails nothing is
+// modified.
+template <class T>
+__device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Trig<T>& g, T dkdw,
+                                                       float R, int max_iter, float tol_abs,
+                                                       unsigned (&iters)[Lanes<T>::n],
+                                                       typename Lanes<T>::M& notconv) {
+  const T x = p[0], y = p[1];
+  const T kappa = dkdw * p[3];
+  PathR<T> w;
+  const auto fail = path_r(p, g, kappa, R, max_iter, tol_abs, iters, notconv, w);
+  if (any(fail)) return fail;
+  const T h = w.h, d = w.d, u = w.u, s = w.s, cu = w.cu, cm = w.cm, sm = w.sm;
+  T px = w.px, py = w.py, c1 = w.c1, s1 = w.s1;
   // The loop evaluated the helix at h - d; move along the tangent by d
   // (the neglected curvature term, kappa d^2 / 2, is below FP32 resolution
   // once |d| <= tol) and turn the direction by kappa d.

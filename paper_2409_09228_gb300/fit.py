@@ -79,7 +79,8 @@ class fit_plan_info(ctypes.Structure):
 
 EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_last_error",
            "fit_propagate_update_noalloc", "fit_plan_create", "fit_plan_run", "fit_plan_tune",
-           "fit_plan_get_info", "fit_plan_destroy")
+           "fit_plan_get_info", "fit_plan_destroy", "fit_tape_bytes", "fit_adjoint_forward",
+           "fit_adjoint_backward")
 FIT_NOALLOC_MAX_EVENTS = 4096
 
 _lib = None
@@ -135,6 +136,17 @@ def load(build_if_missing: bool = True):
     L.fit_plan_get_info.restype = ctypes.c_int
     L.fit_plan_destroy.argtypes = [vp]
     L.fit_plan_destroy.restype = None
+    L.fit_tape_bytes.argtypes = [ctypes.c_int, i64]
+    L.fit_tape_bytes.restype = ctypes.c_size_t
+    L.fit_adjoint_forward.argtypes = [vp, ctypes.POINTER(fit_tracks_in),
+                                      ctypes.POINTER(fit_tracks_out), ctypes.POINTER(fit_hits),
+                                      ctypes.c_int, ctypes.POINTER(i64), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int32), vp, vp]
+    L.fit_adjoint_forward.restype = ctypes.c_int
+    L.fit_adjoint_backward.argtypes = [vp, ctypes.POINTER(fit_hits), ctypes.c_int,
+                                       ctypes.POINTER(i64), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int32), vp, vp, vp, vp, vp, vp]
+    L.fit_adjoint_backward.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -291,6 +303,86 @@ def fit_plan_get_info(plan: int) -> dict:
 def fit_plan_destroy(plan: int) -> None:
     if plan:
         load().fit_plan_destroy(ctypes.c_void_p(plan))
+
+
+def fit_tape_bytes(nlayer: int, ld: int) -> int:
+    return int(load().fit_tape_bytes(nlayer, ld))
+
+
+def _events(ntrk, mode):
+    nt = np.ascontiguousarray(ntrk, dtype=np.int64)
+    md = np.ascontiguousarray(mode, dtype=np.int32)
+    return (len(nt), nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), nt, md)
+
+
+def fit_adjoint_forward(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk, mode, tape, par_out,
+                        cov_out, q_out, chi2, chi2_layer=None, status=None, stream=None) -> None:
+    """The fused fit that also records the per-layer checkpoints in `tape`."""
+    tin, tout, hits = _buffers(par_in, cov_in, q_in, hpos, hcov, par_out, cov_out, q_out, chi2,
+                               chi2_layer, status)
+    nevt, pn, pm, _k1, _k2 = _events(ntrk, mode)
+    _check(load().fit_adjoint_forward(ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout),
+                                      ctypes.byref(hits), nevt, pn, hpos.shape[0], pm,
+                                      _ptr(tape), _stream_handle(stream)))
+
+
+def fit_adjoint_backward(h: int, hpos, hcov, ntrk, mode, tape, grad_chi2, grad_hpos, grad_par0,
+                         grad_cov0=None, stream=None) -> None:
+    """Reverse sweep: gradients of grad_chi2-weighted summed chi2 (see fit.h)."""
+    hits = fit_hits(_ptr(hpos), _ptr(hcov), hpos.shape[-1])
+    nevt, pn, pm, _k1, _k2 = _events(ntrk, mode)
+    _check(load().fit_adjoint_backward(ctypes.c_void_p(h), ctypes.byref(hits), nevt, pn,
+                                       hpos.shape[0], pm, _ptr(tape), _ptr(grad_chi2),
+                                       _ptr(grad_hpos), _ptr(grad_par0), _ptr(grad_cov0),
+                                       _stream_handle(stream)))
+
+
+def _chi2_function():
+    import torch
+
+    class Chi2(torch.autograd.Function):
+        """chi2 per track of the fused fit, differentiable in the hit positions
+        and the initial parameters and covariance (hand-written adjoint)."""
+
+        @staticmethod
+        def forward(ctx, hpos, par0, cov0, q, hcov, fitter, ntrk, mode):
+            ld, nlayer = hpos.shape[-1], hpos.shape[0]
+            tape = torch.empty(fit_tape_bytes(nlayer, ld) // 4, dtype=torch.float32,
+                               device=hpos.device)
+            out = fitter.outputs(int(np.sum(ntrk)), ld=ld)
+            fit_adjoint_forward(fitter.h, par0, cov0, q, hpos, hcov, ntrk, mode, tape,
+                                out["par"], out["cov"], out["q"], out["chi2"],
+                                status=out["status"])
+            ctx.save_for_backward(hpos, hcov, tape)
+            ctx.fitter, ctx.ntrk, ctx.mode = fitter, list(ntrk), list(mode)
+            ctx.mark_non_differentiable(out["par"], out["cov"])
+            return out["chi2"], out["par"], out["cov"]
+
+        @staticmethod
+        def backward(ctx, grad_chi2, _gpar, _gcov):
+            hpos, hcov, tape = ctx.saved_tensors
+            ld = hpos.shape[-1]
+            g_hpos = torch.empty_like(hpos)
+            g_par0 = torch.empty((6, ld), dtype=torch.float32, device=hpos.device)
+            g_cov0 = torch.empty((21, ld), dtype=torch.float32, device=hpos.device)
+            fit_adjoint_backward(ctx.fitter.h, hpos, hcov, ctx.ntrk, ctx.mode, tape,
+                                 grad_chi2.contiguous(), g_hpos, g_par0, g_cov0)
+            return g_hpos, g_par0, g_cov0, None, None, None, None, None
+
+    return Chi2
+
+
+_CHI2 = None
+
+
+def chi2(fitter: "Fitter", hpos, par0, cov0, q, hcov, ntrk, mode):
+    """(chi2 per track, fitted par, fitted cov) with autograd through chi2 to
+    hpos, par0 and cov0."""
+    global _CHI2
+    if _CHI2 is None:
+        _CHI2 = _chi2_function()
+    return _CHI2.apply(hpos, par0, cov0, q, hcov, fitter, ntrk, mode)
 
 
 def fit_sync(h: int, stream=None, timeout_s: float = 0.0) -> dict:
