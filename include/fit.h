@@ -279,6 +279,118 @@ int fit_adjoint_backward(fit_handle* h, const fit_hits* hits, int nevt, const in
                          int nlayer, const int32_t* mode, const void* tape, const float* grad_chi2,
                          float* grad_hpos, float* grad_par0, float* grad_cov0, void* stream);
 
+/*
+ * Learned path-length seed for p2r.  The paper's p2r finds the path length to
+ * the cylinder by discrete straight-line steps (Sec. 3.2); these entry points
+ * add a small network, 8 -> 64 -> 64 -> 1 with ReLU, BF16 weights and FP32
+ * accumulation on the tensor cores, whose output starts that iteration closer
+ * to the root.  The iteration then runs exactly as without it (same
+ * tolerance, same result within it): the network only changes where it
+ * starts, and a seed that is not finite or further than a quarter of the
+ * straight-line distance from it is replaced by the straight-line seed.  The
+ * paper has no network; this is an addition.
+ *
+ * Inputs of one sample (a track state p, charge q, target radius R), in the
+ * frame whose x axis points along the track's transverse position:
+ *   x[0] = r0 / R, x[1] = z / R, x[2] = kA B w R / 2, x[3] = cos psi,
+ *   x[4] = sin psi, x[5] = cos theta, x[6] = q, x[7] = R / 100 cm,
+ * with r0 = sqrt(x^2 + y^2), psi = phi - atan2(y, x), kA = 0.00299792458.
+ * Target: g = (h - h_line) / (kappa h_line^2 / 2), h the exact transverse path
+ * length, h_line the straight-line distance along the momentum to the
+ * cylinder, kappa = -q kA B w; the seed is h_line + g kappa h_line^2 / 2.
+ *
+ * Parameters: FIT_MLP_PARAMS floats, W1[64][8], b1[64], W2[64][64], b2[64],
+ * W3[64], b3 (W[out][in]); the master copy is FP32, the forward pass rounds
+ * weights and activations to BF16 (round to nearest even) and each input to a
+ * pair of BF16 numbers hi = bf16(x), lo = bf16(x - hi).
+ */
+#define FIT_MLP_INPUTS 8
+#define FIT_MLP_HIDDEN 64
+#define FIT_MLP_PARAMS 4801
+
+typedef struct fit_mlp fit_mlp;
+
+typedef struct {
+  int epochs;      /* passes over the samples */
+  int batch;       /* samples per Adam step, 64..65536 */
+  float lr;        /* learning rate of the first step ... */
+  float lr_final;  /* ... decayed along a half cosine to this at the last */
+  float beta1, beta2, eps; /* Adam (Kingma and Ba, 2015) */
+  uint64_t seed;   /* order of the batches */
+} fit_mlp_train_config;
+
+/*
+ * fit_mlp_create: a network on `device` with He-uniform weights drawn from
+ * `seed` and zero biases; Adam state zero.  fit_mlp_destroy frees it.
+ */
+int fit_mlp_create(fit_mlp** m, int device, uint64_t seed);
+void fit_mlp_destroy(fit_mlp* m);
+
+/* fit_mlp_set_params / get_params: the FP32 master parameters, HOST arrays of
+ * FIT_MLP_PARAMS floats.  set_params also resets the Adam state. */
+int fit_mlp_set_params(fit_mlp* m, const float* params);
+int fit_mlp_get_params(const fit_mlp* m, float* params);
+
+/*
+ * fit_mlp_prepare: the inputs x (DEVICE, [n][8] row-major) of n samples --
+ * states par ([6][ld], track fastest), charges q [n], target radii R [n] --
+ * for field B; with h_exact (DEVICE [n], the exact path lengths) also the
+ * targets (DEVICE [n]); a sample with no straight-line crossing from inside
+ * the cylinder, or kappa = 0, gets a NaN target, which training skips.
+ */
+int fit_mlp_prepare(float B, const float* par, int64_t ld, const int32_t* q, const float* R,
+                    const float* h_exact, int64_t n, float* x, float* target, void* stream);
+
+/* fit_mlp_forward: the network's output y [n] (DEVICE) for inputs x [n][8]. */
+int fit_mlp_forward(const fit_mlp* m, const float* x, int64_t n, float* y, void* stream);
+
+/*
+ * fit_mlp_gradient: the gradient (DEVICE [FIT_MLP_PARAMS]) of the mean squared
+ * error L = (1/n) sum_i (y_i - target_i)^2 over the n samples with finite
+ * targets (the rounding to BF16 passes gradients through unchanged), and L
+ * itself (DEVICE [1]).  1 <= n <= 65536.
+ */
+int fit_mlp_gradient(fit_mlp* m, const float* x, const float* target, int64_t n, float* grad,
+                     float* loss, void* stream);
+
+/* fit_mlp_adam_step: one Adam update of the master parameters with the
+ * gradient grad (DEVICE), learning rate lr and the network's Adam settings
+ * (beta1 0.9, beta2 0.999, eps 1e-8 unless fit_mlp_train set others). */
+int fit_mlp_adam_step(fit_mlp* m, const float* grad, float lr, void* stream);
+
+/*
+ * fit_mlp_train: minimises the mean squared error of the network's output
+ * against the targets by Adam over `epochs` passes of batches of cfg->batch
+ * consecutive samples (from a per-epoch offset drawn from cfg->seed; n must
+ * be >= cfg->batch).  Each step is one forward+backward kernel and one Adam
+ * kernel on `stream`.  loss_per_epoch (HOST [epochs], may be NULL) receives the
+ * mean training loss of each epoch; the call then waits for the stream.
+ */
+int fit_mlp_train(fit_mlp* m, const float* x, const float* target, int64_t n,
+                  const fit_mlp_train_config* cfg, float* loss_per_epoch, void* stream);
+
+/*
+ * fit_mlp_attach: the handle's p2r fits (fit_propagate_update) and
+ * fit_path_lengths seed from the network's current weights (a copy taken on
+ * `stream`); m = NULL detaches.  An attached handle runs p2r with one track
+ * per thread so that each warp evaluates the network on its 32 tracks
+ * together; fit_plan_*, fit_adjoint_* and fit_propagate_update_noalloc do
+ * not use the seed.
+ */
+int fit_mlp_attach(fit_handle* h, const fit_mlp* m, void* stream);
+
+/*
+ * fit_path_lengths: the p2r path-length iteration alone, for n independent
+ * states par ([6][ld]) with charges q [n] to their own radii R [n], with the
+ * handle's p2r tolerance and iteration limit: h_out [n] the path length
+ * (NaN when the cylinder is not reached), iters_out [n] (may be NULL) the
+ * iterations taken.  seeded = 1 starts from the attached network (FIT_ERR_ARG
+ * if none), 0 from the straight line.  All DEVICE.
+ */
+int fit_path_lengths(fit_handle* h, const float* par, int64_t ld, const int32_t* q,
+                     const float* R, int64_t n, float* h_out, int32_t* iters_out, int seeded,
+                     void* stream);
+
 /* fit_destroy: frees the handle and its scratch (after pending work ends). */
 void fit_destroy(fit_handle* h);
 

@@ -82,6 +82,8 @@ class Oracle:
         L.orc_update.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D, _I, _D]
         L.orc_fit.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, ctypes.c_int64,
                               _D, _D, _I, _D, _D, _D, _D, _I, _D, _D, _U8, ctypes.c_int]
+        L.orc_path_lengths.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64, _D, _I, _D,
+                                       _D, _U8, ctypes.c_int]
         L.orc_chi2_grad.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _D,
                                     ctypes.c_int64, _D, _D, _I, _D, _D, _D, _D, _D, _U8,
                                     ctypes.c_int]
@@ -101,6 +103,15 @@ class Oracle:
         h = np.zeros(1)
         st = self.L.orc_path_length(mode, B, s, int(q), _p(p), _p(h))
         return st, float(h[0])
+
+    def path_lengths(self, mode: int, B: float, s, q, p, nthreads: int = 0):
+        """(h, status) for n states p (6, n) with charges q (n,) to surfaces s (n,)."""
+        s, p = _d(s), _d(p)
+        q = np.ascontiguousarray(q, dtype=np.int32)
+        n = p.shape[1]
+        h, st = np.zeros(n), np.zeros(n, np.uint8)
+        self.L.orc_path_lengths(mode, B, n, _p(s), _p(q, _I), _p(p), _p(h), _p(st, _U8), nthreads)
+        return h, st
 
     def transport(self, mode: int, B: float, s: float, q: int, p):
         """(status, p_out, J (6x6), h) of the propagate-to-surface map."""
@@ -185,6 +196,10 @@ def path_length(*a, **k):
 
 def transport(*a, **k):
     return default().transport(*a, **k)
+
+
+def path_lengths(*a, **k):
+    return default().path_lengths(*a, **k)
 
 
 def propagate(*a, **k):

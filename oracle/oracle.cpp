@@ -462,6 +462,20 @@ int orc_update(int mode, int q, const double* p, const double* cov, const double
   return (int)st;
 }
 
+// Exact transverse path length of n independent states (p [6][n], charge
+// q [n]) to their own surface s [n] (radius or z): h [n], status [n].
+int orc_path_lengths(int mode, double B, int64_t n, const double* s, const int* q,
+                     const double* p, double* h, unsigned char* status, int nthreads) {
+  parallel_for(n, nthreads, [&](int64_t i) {
+    double pi[6];
+    for (int k = 0; k < 6; ++k) pi[k] = p[k * n + i];
+    double hi = 0.0;
+    status[i] = (unsigned char)path_length(mode, pi, q[i], B, s[i], hi);
+    h[i] = hi;
+  });
+  return 0;
+}
+
 // Full fit of n tracks over nlayer surfaces.  Layouts (track index fastest,
 // stride n): par0/par [6][n], cov0/cov [21][n], q0/q [n], hpos [nlayer][3][n],
 // hcov [nlayer][6][n], chi2 [n], chi2_layer [nlayer][n] (may be NULL),

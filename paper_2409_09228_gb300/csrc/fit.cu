@@ -248,9 +248,11 @@ int fit_propagate_update(fit_handle* h, const fit_tracks_in* in, const fit_track
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   rc = launch_segments(h, base_args(in, out, hits, nlayer, h->d_counters), nevt, ntrk, mode,
                        "fit_propagate_update",
-                       [s](const FitArgs& a, int m, unsigned nblk, int, int) {
+                       [s, h](const FitArgs& a, int m, unsigned nblk, int, int) {
                          if (m == FIT_MODE_Z)
                            fit_fused_kernel<FIT_MODE_Z><<<nblk, kBlock, 0, s>>>(a);
+                         else if (h->seeded)
+                           launch_seeded_fit(a, h->d_mlp, s);
                          else
                            fit_fused_kernel<FIT_MODE_R><<<nblk, kBlock, 0, s>>>(a);
                        });
@@ -359,10 +361,9 @@ void fit_destroy(fit_handle* h) {
   if (!h) return;
   {
     DeviceGuard g(h->device);
-    if (h->d_counters) {
-      cudaDeviceSynchronize();
-      cudaFree(h->d_counters);
-    }
+    if (h->d_counters || h->d_mlp) cudaDeviceSynchronize();
+    if (h->d_counters) cudaFree(h->d_counters);
+    if (h->d_mlp) cudaFree(h->d_mlp);
   }
   delete h;
 }

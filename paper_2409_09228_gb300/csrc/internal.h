@@ -78,6 +78,8 @@ struct fit_handle {
   fitimpl::Geo geo[2];
   unsigned long long* d_counters = nullptr;  // [kCounters]
   uint64_t tracks = 0;
+  void* d_mlp = nullptr;  // learned-seed weights (fit_mlp_attach), device
+  bool seeded = false;    // p2r seeds from d_mlp
 };
 
 
@@ -89,5 +91,9 @@ int check_call(const fit_handle* h, const fit_tracks_in* in, const fit_tracks_ou
                const int32_t* mode, int64_t* total_out, const char* who);
 FitArgs base_args(const fit_tracks_in* in, const fit_tracks_out* out, const fit_hits* hits,
                   int nlayer, unsigned long long* counters);
+
+// The p2r fit seeded by the learned path length (mlp.cu), one track per
+// thread over a.t0 .. a.t1; img is the handle's d_mlp.
+void launch_seeded_fit(const FitArgs& a, const void* img, cudaStream_t s);
 
 }  // namespace fitimpl

@@ -278,11 +278,18 @@ struct PathR {
   T h, d, u, s, cu, cm, sm, px, py, c1, s1;
 };
 
-template <class T>
+//
+// SEEDED: gseed is the learned seed's output g (mlp.cuh); the iteration starts
+// at h_line + g kappa h_line^2 / 2 instead of the straight-line distance
+// h_line when the start is inside the cylinder and that value is finite and
+// within h_line / 4 of h_line.  The iteration, its tolerance and its result
+// are otherwise unchanged.
+template <class T, bool SEEDED = false>
 __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Trig<T>& g, T kappa,
                                                        float R, int max_iter, float tol_abs,
                                                        unsigned (&iters)[Lanes<T>::n],
-                                                       typename Lanes<T>::M& notconv, PathR<T>& w) {
+                                                       typename Lanes<T>::M& notconv, PathR<T>& w,
+                                                       T gseed = T(0.f)) {
   using M = typename Lanes<T>::M;
   const T sph = g.sphi, cph = g.cphi;
   const T x = p[0], y = p[1];
@@ -305,6 +312,10 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
   fail = or_(fail, or_(lt(disc0, T(0.f)), and_(not_(inside), not_(lt(b0, T(0.f))))));
   if (any(fail)) return fail;
   T h = sel(inside, sel(lt(T(0.f), b0), fdiv(-c0, b0 + sq0), sq0 - b0), fdiv(c0, sq0 - b0));
+  if constexpr (SEEDED) {
+    const T hs = fma(gseed * T(0.5f) * kappa, h * h, h);
+    h = sel(and_(and_(inside, finite_(hs)), le(fabs_(hs - h), T(0.25f) * h)), hs, h);
+  }
   // The directions phi + u and phi + 2u come from turning (cos phi, sin phi)
   // by u.  A lane that has converged keeps its h.
   M conv = lt(T(1.f), T(0.f));  // all false
@@ -343,15 +354,17 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
 // Propagation to the cylinder r = R (path length from path_r).  Returns the
 // mask of lanes that cannot reach the cylinder; if any lane fails nothing is
 // modified.
-template <class T>
+template <class T, bool SEEDED = false>
 __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Trig<T>& g, T dkdw,
                                                        float R, int max_iter, float tol_abs,
                                                        unsigned (&iters)[Lanes<T>::n],
-                                                       typename Lanes<T>::M& notconv) {
+                                                       typename Lanes<T>::M& notconv,
+                                                       T gseed = T(0.f)) {
   const T x = p[0], y = p[1];
   const T kappa = dkdw * p[3];
   PathR<T> w;
-  const auto fail = path_r(p, g, kappa, R, max_iter, tol_abs, iters, notconv, w);
+  const auto fail =
+      path_r<T, SEEDED>(p, g, kappa, R, max_iter, tol_abs, iters, notconv, w, gseed);
   if (any(fail)) return fail;
   const T h = w.h, d = w.d, u = w.u, s = w.s, cu = w.cu, cm = w.cm, sm = w.sm;
   T px = w.px, py = w.py, c1 = w.c1, s1 = w.s1;

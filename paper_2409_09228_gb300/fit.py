@@ -77,10 +77,21 @@ class fit_plan_info(ctypes.Structure):
                 ("items", ctypes.c_int32), ("tuned", ctypes.c_int32), ("best_ms", ctypes.c_float)]
 
 
+class fit_mlp_train_config(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
+                ("lr_final", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
 EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_last_error",
            "fit_propagate_update_noalloc", "fit_plan_create", "fit_plan_run", "fit_plan_tune",
            "fit_plan_get_info", "fit_plan_destroy", "fit_tape_bytes", "fit_adjoint_forward",
-           "fit_adjoint_backward")
+           "fit_adjoint_backward", "fit_mlp_create", "fit_mlp_destroy", "fit_mlp_set_params",
+           "fit_mlp_get_params", "fit_mlp_prepare", "fit_mlp_forward", "fit_mlp_gradient",
+           "fit_mlp_adam_step", "fit_mlp_train", "fit_mlp_attach", "fit_path_lengths")
+FIT_MLP_INPUTS = 8
+FIT_MLP_HIDDEN = 64
+FIT_MLP_PARAMS = 4801
 FIT_NOALLOC_MAX_EVENTS = 4096
 
 _lib = None
@@ -147,6 +158,29 @@ def load(build_if_missing: bool = True):
                                        ctypes.POINTER(i64), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int32), vp, vp, vp, vp, vp, vp]
     L.fit_adjoint_backward.restype = ctypes.c_int
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.fit_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_uint64]
+    L.fit_mlp_create.restype = ctypes.c_int
+    L.fit_mlp_destroy.argtypes = [vp]
+    L.fit_mlp_destroy.restype = None
+    L.fit_mlp_set_params.argtypes = [vp, vp]
+    L.fit_mlp_set_params.restype = ctypes.c_int
+    L.fit_mlp_get_params.argtypes = [vp, vp]
+    L.fit_mlp_get_params.restype = ctypes.c_int
+    L.fit_mlp_prepare.argtypes = [ctypes.c_float, vp, i64, vp, vp, vp, i64, vp, vp, vp]
+    L.fit_mlp_prepare.restype = ctypes.c_int
+    L.fit_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+    L.fit_mlp_forward.restype = ctypes.c_int
+    L.fit_mlp_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    L.fit_mlp_gradient.restype = ctypes.c_int
+    L.fit_mlp_adam_step.argtypes = [vp, vp, ctypes.c_float, vp]
+    L.fit_mlp_adam_step.restype = ctypes.c_int
+    L.fit_mlp_train.argtypes = [vp, vp, vp, i64, ctypes.POINTER(fit_mlp_train_config), vp, vp]
+    L.fit_mlp_train.restype = ctypes.c_int
+    L.fit_mlp_attach.argtypes = [vp, vp, vp]
+    L.fit_mlp_attach.restype = ctypes.c_int
+    L.fit_path_lengths.argtypes = [vp, vp, i64, vp, vp, i64, vp, i32p, ctypes.c_int, vp]
+    L.fit_path_lengths.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -383,6 +417,82 @@ def chi2(fitter: "Fitter", hpos, par0, cov0, q, hcov, ntrk, mode):
     if _CHI2 is None:
         _CHI2 = _chi2_function()
     return _CHI2.apply(hpos, par0, cov0, q, hcov, fitter, ntrk, mode)
+
+
+# ---- learned path-length seed (p2r) -------------------------------------------------
+
+
+def fit_mlp_create(device: int = 0, seed: int = 1) -> int:
+    m = ctypes.c_void_p()
+    _check(load().fit_mlp_create(ctypes.byref(m), int(device), int(seed)))
+    return m.value
+
+
+def fit_mlp_destroy(m: int) -> None:
+    if m:
+        load().fit_mlp_destroy(ctypes.c_void_p(m))
+
+
+def fit_mlp_set_params(m: int, params) -> None:
+    """params: FIT_MLP_PARAMS floats (host), W1, b1, W2, b2, W3, b3."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.shape != (FIT_MLP_PARAMS,):
+        raise ValueError(f"expected {FIT_MLP_PARAMS} parameters, got {p.shape}")
+    _check(load().fit_mlp_set_params(ctypes.c_void_p(m), p.ctypes.data))
+
+
+def fit_mlp_get_params(m: int) -> np.ndarray:
+    p = np.empty(FIT_MLP_PARAMS, np.float32)
+    _check(load().fit_mlp_get_params(ctypes.c_void_p(m), p.ctypes.data))
+    return p
+
+
+def fit_mlp_prepare(B: float, par, q, R, x, h_exact=None, target=None, n: Optional[int] = None,
+                    stream=None) -> None:
+    """Network inputs x (n, 8) (and targets from h_exact) of states par (6, ld)."""
+    n = R.shape[0] if n is None else n
+    _check(load().fit_mlp_prepare(float(B), _ptr(par), par.shape[-1], _ptr(q), _ptr(R),
+                                  _ptr(h_exact), n, _ptr(x), _ptr(target), _stream_handle(stream)))
+
+
+def fit_mlp_forward(m: int, x, y, stream=None) -> None:
+    _check(load().fit_mlp_forward(ctypes.c_void_p(m), _ptr(x), x.shape[0], _ptr(y),
+                                  _stream_handle(stream)))
+
+
+def fit_mlp_gradient(m: int, x, target, grad, loss, stream=None) -> None:
+    _check(load().fit_mlp_gradient(ctypes.c_void_p(m), _ptr(x), _ptr(target), x.shape[0],
+                                   _ptr(grad), _ptr(loss), _stream_handle(stream)))
+
+
+def fit_mlp_adam_step(m: int, grad, lr: float, stream=None) -> None:
+    _check(load().fit_mlp_adam_step(ctypes.c_void_p(m), _ptr(grad), float(lr),
+                                    _stream_handle(stream)))
+
+
+def fit_mlp_train(m: int, x, target, epochs: int, batch: int = 4096, lr: float = 2e-3,
+                  lr_final: float = 1e-5, beta1: float = 0.9, beta2: float = 0.999,
+                  eps: float = 1e-8, seed: int = 1, stream=None) -> np.ndarray:
+    """Adam on the mean squared error; returns the mean loss of each epoch."""
+    cfg = fit_mlp_train_config(int(epochs), int(batch), float(lr), float(lr_final), float(beta1),
+                               float(beta2), float(eps), int(seed))
+    curve = np.zeros(int(epochs), np.float32)
+    _check(load().fit_mlp_train(ctypes.c_void_p(m), _ptr(x), _ptr(target), x.shape[0],
+                                ctypes.byref(cfg), curve.ctypes.data, _stream_handle(stream)))
+    return curve
+
+
+def fit_mlp_attach(h: int, m: Optional[int], stream=None) -> None:
+    _check(load().fit_mlp_attach(ctypes.c_void_p(h), ctypes.c_void_p(m) if m else None,
+                                 _stream_handle(stream)))
+
+
+def fit_path_lengths(h: int, par, q, R, h_out, iters_out=None, seeded: bool = False,
+                     n: Optional[int] = None, stream=None) -> None:
+    n = R.shape[0] if n is None else n
+    it = None if iters_out is None else ctypes.cast(_ptr(iters_out), ctypes.POINTER(ctypes.c_int32))
+    _check(load().fit_path_lengths(ctypes.c_void_p(h), _ptr(par), par.shape[-1], _ptr(q), _ptr(R),
+                                   n, _ptr(h_out), it, int(bool(seeded)), _stream_handle(stream)))
 
 
 def fit_sync(h: int, stream=None, timeout_s: float = 0.0) -> dict:

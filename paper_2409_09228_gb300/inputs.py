@@ -93,6 +93,16 @@ class TrackSet:
                         None if self.truth is None else np.ascontiguousarray(self.truth[:, :, idx]))
 
 
+def _p2r_crossing(s, rho, phi0, q, cot):
+    """Where a truth helix from the origin crosses the cylinder of radius s: a
+    circle through the origin reaches radius s after turning by
+    2 asin(s / 2 rho), and the crossing sits on the chord direction.  Returns
+    (azimuth of the crossing, its z, momentum azimuth there)."""
+    with np.errstate(invalid="ignore"):
+        half = np.arcsin(s / (2.0 * rho))
+    return phi0 - q * half, 2.0 * rho * half * cot, phi0 - 2.0 * q * half
+
+
 def generate(mode: int, n: int, seed: int, nlayer: int = NLAYER, B: float = B_FIELD,
              surf: Optional[np.ndarray] = None, pt_range=(0.5, 10.0), eta_range=None,
              want_truth: bool = False, sigma_rphi: float = SIGMA_RPHI,
@@ -131,13 +141,7 @@ def generate(mode: int, n: int, seed: int, nlayer: int = NLAYER, B: float = B_FI
         n1 = noise.standard_normal(n)
         n2 = noise.standard_normal(n)
         if mode == MODE_R:
-            # A circle through the origin reaches radius R after turning by
-            # 2 asin(R / 2 rho); the crossing sits on the chord direction.
-            with np.errstate(invalid="ignore"):
-                half = np.arcsin(s / (2.0 * rho))
-            h = 2.0 * rho * half
-            chord_phi = phi0 - q * half
-            z = h * cot
+            chord_phi, z, phi_dir = _p2r_crossing(s, rho, phi0, q, cot)
             phi_hit = chord_phi + n1 * sigma_rphi / s
             c, sn = np.cos(phi_hit), np.sin(phi_hit)
             hpos[l, 0], hpos[l, 1], hpos[l, 2] = s * c, s * sn, z + n2 * sigma_2
@@ -147,8 +151,7 @@ def generate(mode: int, n: int, seed: int, nlayer: int = NLAYER, B: float = B_FI
             hcov[l, 2] = vr * c * c
             hcov[l, 5] = sigma_2 ** 2
             if want_truth:
-                truth[l] = (s * np.cos(chord_phi), s * np.sin(chord_phi), z, w,
-                            phi0 - 2.0 * q * half, theta)
+                truth[l] = (s * np.cos(chord_phi), s * np.sin(chord_phi), z, w, phi_dir, theta)
         else:
             # Transverse path to the plane, then the chord of that arc.
             h = s * np.tan(theta)
@@ -178,6 +181,57 @@ def generate(mode: int, n: int, seed: int, nlayer: int = NLAYER, B: float = B_FI
     for i in range(6):
         cov0[i * (i + 1) // 2 + i] = (sig[i] ** 2).astype(np.float32)
     return TrackSet(mode, B, surf, par0, cov0, q, hpos, hcov, truth)
+
+
+# Spread of a filtered state around the truth, used for the learned seed's
+# samples: position (x, y, z) in cm, relative w, phi and theta in rad.
+SIGMA_STATE = (0.01, 0.01, 0.1, 0.01, 1e-3, 1e-3)
+
+
+@dataclass
+class SeedSamples:
+    """Single p2r propagations: state par (6, n) float32 with charge q (n,)
+    int32, to the cylinder of radius R (n,) float32, layer index layer (n,)."""
+    B: float
+    par: np.ndarray
+    q: np.ndarray
+    R: np.ndarray
+    layer: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return self.par.shape[1]
+
+
+def seed_samples(n: int, seed: int, nlayer: int = NLAYER, B: float = B_FIELD,
+                 surf: Optional[np.ndarray] = None) -> SeedSamples:
+    """Samples of the propagations a p2r fit makes: a track drawn as in
+    generate(MODE_R, ...), a layer l uniform in [0, nlayer), the cylinder R_l as
+    target, and as start the state the fit would hold before layer l -- the
+    smeared vertex state for l = 0, else the truth crossing of layer l - 1
+    smeared by SIGMA_STATE (the spread of a filtered state)."""
+    surf = surfaces(MODE_R, nlayer) if surf is None else np.asarray(surf, np.float32)
+    nlayer = surf.shape[0]
+    B = float(np.float32(B))
+    lo = max(0.5, pt_min_p2r(B, float(surf.astype(np.float64).max())))
+    pt = _rng(seed, _STREAM_PT).uniform(lo, 10.0, n)
+    eta = _rng(seed, _STREAM_ETA).uniform(-1.0, 1.0, n)
+    phi0 = _rng(seed, _STREAM_PHI).uniform(0.0, 2.0 * np.pi, n)
+    q = np.where(_rng(seed, _STREAM_Q).random(n) < 0.5, -1, 1).astype(np.int32)
+    layer = _rng(seed, 18).integers(0, nlayer, n)
+    theta = 2.0 * np.arctan(np.exp(-eta))
+    w = 1.0 / pt
+    rho = pt / (KA * B)
+    s_prev = surf.astype(np.float64)[np.maximum(layer - 1, 0)]
+    chord_phi, z, phi_dir = _p2r_crossing(s_prev, rho, phi0, q, 1.0 / np.tan(theta))
+    on_layer = np.stack([s_prev * np.cos(chord_phi), s_prev * np.sin(chord_phi), z, w, phi_dir,
+                         theta])
+    at_vertex = np.stack([np.zeros(n), np.zeros(n), np.zeros(n), w, phi0, theta])
+    sig_v = np.array(SIGMA0)[:, None] * np.stack([np.ones(n)] * 3 + [w] + [np.ones(n)] * 2)
+    sig_l = np.array(SIGMA_STATE)[:, None] * np.stack([np.ones(n)] * 3 + [w] + [np.ones(n)] * 2)
+    noise = _rng(seed, _STREAM_INIT).standard_normal((6, n))
+    par = np.where(layer[None, :] == 0, at_vertex + sig_v * noise, on_layer + sig_l * noise)
+    return SeedSamples(B, par.astype(np.float32), q, surf[layer], layer.astype(np.int32))
 
 
 def uneven_event_sizes(nevt: int, seed: int, median: float = 2000.0, sigma_ln: float = 1.0,
