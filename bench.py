@@ -358,6 +358,164 @@ def bench_adjoint(args, world, rank, local):
     print(json.dumps(line))
 
 
+def bench_seed(args, world, rank, local):
+    """The learned p2r path-length seed.  Trains the network on 4M single p2r
+    propagations labelled by the library's own exact iteration (run to
+    1e-7 R), then fits 1M p2r tracks x 20 layers with the straight-line seed
+    (the packed two-tracks-per-thread kernel) and with the network (one track
+    per thread, the network before every layer), and times the path-length
+    step alone on 4M states with each seed.  The value is the seeded fit's
+    throughput; the line carries the plain fit's beside it."""
+    import torch
+    from paper_2409_09228_gb300 import fit, inputs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    surf = inputs.surfaces(inputs.MODE_R)
+
+    # training data: exact path lengths from the iteration itself, tight tolerance
+    lab = fit.Fitter(fit.Geometry(inputs.B_FIELD, surf, max_iter=30, tol=1e-7), None, device=local)
+
+    def labelled(nsamp, seed):
+        ss = inputs.seed_samples(nsamp, seed=seed)
+        par, q, R = up(ss.par), up(ss.q), up(ss.R)
+        h = torch.empty(nsamp, device=dev)
+        fit.fit_path_lengths(lab.h, par, q, R, h, stream=stream)
+        x = torch.empty((nsamp, 8), device=dev)
+        t = torch.empty(nsamp, device=dev)
+        fit.fit_mlp_prepare(ss.B, par, q, R, x, h_exact=h, target=t, stream=stream)
+        return ss, par, q, R, h, x, t
+
+    _, _, _, _, _, x, t = labelled(args.seed_train_samples, 4)
+    m = fit.fit_mlp_create(local, seed=4)
+    t0 = time.perf_counter()
+    curve = fit.fit_mlp_train(m, x, t, epochs=args.seed_epochs, batch=4096, lr=2e-3,
+                              lr_final=1e-6, seed=4, stream=stream)
+    train_s = time.perf_counter() - t0
+    del x, t
+    f = fit.Fitter(fit.Geometry(inputs.B_FIELD, surf), None, device=local)
+    fit.fit_mlp_attach(f.h, m, stream=stream)
+    # the path-length step alone, held-out states
+    ss, par, q, R, h_ex, xe, _ = labelled(4_000_000, 400 + 1000 * rank)
+    ye = torch.empty(ss.n, device=dev)
+    fit.fit_mlp_forward(m, xe, ye, stream=stream)
+    hl = torch.empty(ss.n, device=dev)
+    its = torch.empty(ss.n, dtype=torch.int32, device=dev)
+
+    def step_alone(seeded):
+        fit.fit_path_lengths(f.h, par, q, R, hl, its, seeded=seeded, stream=stream)
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    alone = {}
+    for seeded in (False, True):
+        ms = timed(lambda: step_alone(seeded), args.steps)
+        alone["network" if seeded else "straight_line"] = {
+            "ms": ms, "iterations_per_state": float(its.double().mean().item()),
+            "one_iteration": float((its == 1).double().mean().item()),
+            "max_abs_dh_vs_1e-7_iteration_cm": float((hl - h_ex).abs().max().item())}
+    seed_err = None
+    # seed error of the held-out states in units of the tolerance 1e-6 R
+    with torch.no_grad():
+        kB = inputs.KA * float(np.float32(inputs.B_FIELD))
+        x0, y0, ph = par[0].double(), par[1].double(), par[4].double()
+        b = x0 * torch.cos(ph) + y0 * torch.sin(ph)
+        c = x0 * x0 + y0 * y0 - R.double() ** 2
+        hline = -b + torch.sqrt(b * b - c)
+        kap = -q.double() * kB * par[3].double()
+        hs = hline + ye.double() * 0.5 * kap * hline * hline
+        e = ((hs - h_ex.double()).abs() / (1e-6 * R.double())).cpu().numpy()
+        seed_err = {"median_over_tol": float(np.median(e)), "within_tol": float(np.mean(e <= 1)),
+                    "p99_over_tol": float(np.quantile(e, 0.99))}
+    del xe, ye, hl, its, par, q, R, h_ex
+    lab.close()
+
+    # the fit: 1M tracks x 20 layers, plain and seeded
+    n = args.seed_tracks
+    ts = inputs.generate(inputs.MODE_R, n, seed=4 + 1000 * rank)
+    ld = (n + 3) // 4 * 4
+    pad = lambda a: up(np.pad(a, [(0, 0)] * (a.ndim - 1) + [(0, ld - n)]))  # noqa: E731
+    d = [pad(a) for a in (ts.par0, ts.cov0, ts.q, ts.hpos, ts.hcov)]
+    out = f.outputs(n, ld=ld)
+    res = {}
+    clk = None
+    for label, net in (("straight_line", None), ("network", m)):
+        fit.fit_mlp_attach(f.h, net, stream=stream)
+        for _ in range(args.warmup):
+            f.run(*d, [n], [0], out=out, stream=stream)
+        f.sync(stream)
+        barrier(world)
+        if net is not None:
+            clocks = ClockSampler(local)
+            clocks.start()
+            time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            f.run(*d, [n], [0], out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if net is not None:
+            clk = clocks.stop()
+        st = f.sync(stream)
+        assert st["nonfinite"] == 0 and st["no_intersection"] == 0 and st["not_converged"] == 0, st
+        ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
+        res[label] = {"ms": ms, "value": world * n * NLAYER / (ms / 1e3),
+                      "iterations_per_track_layer": st["iterations"] / (args.steps * n * NLAYER)}
+    f.close()
+    fit.fit_mlp_destroy(m)
+    if rank != 0:
+        return
+    ms = res["network"]["ms"]
+    tl = n * NLAYER
+    peaks = load_peaks()
+    alu_peak = fp32_peak_tflops(peaks["sm_max_mhz"])
+    alu_ach = FLOPS_P2R * tl / (ms / 1e3) / 1e12
+    mlp_flops = 2.0 * 4801  # multiply-adds of the network per track-layer, x 2
+    line = {"metric": "track-layer propagate+update/s", "value": res["network"]["value"],
+            "unit": "track-layer/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (network: bf16 in, f32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"learned p2r seed: {n} p2r tracks x {NLAYER} layers, network "
+                                   f"8-64-64-1 trained on {args.seed_train_samples} propagations",
+                       "inputs_exceed_l2": True},
+            "roofline": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": alu_ach / alu_peak, "traffic": None, "kernel": "fit_seeded_kernel",
+                         "flops_per_track_layer": FLOPS_P2R,
+                         "network_tensor_tflops": mlp_flops * tl / (ms / 1e3) / 1e12},
+            "clocks": clk, "gpu_launches": args.steps,
+            "plain_fit": res["straight_line"], "seeded_fit": res["network"],
+            "path_length_step_alone_4M_states": alone, "held_out_seed_error": seed_err,
+            "training": {"samples": args.seed_train_samples, "epochs": args.seed_epochs,
+                         "batch": 4096, "seconds": train_s, "final_loss": float(curve[-1])}}
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cores = len(os.sched_getaffinity(0))
+        done, k, t0 = 0, 0, time.perf_counter()
+        while k * 50000 < n and time.perf_counter() - t0 < 10.0:
+            sub = ts.subset(np.arange(k * 50000, min(n, (k + 1) * 50000)))
+            oracle.fit_set(sub, nthreads=cores)
+            done += sub.n * NLAYER
+            k += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / dt, "unit": "track-layer/s", "cores": cores,
+                                "kind": "oracle", "sample": f"{done // NLAYER} of {n} tracks "
+                                f"(exact FP64 path lengths, no seed), {dt:.1f} s"}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -367,11 +525,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--nevt", type=int, default=NEVT, help="events per mode (default 100)")
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven", "adjoint"],
+    ap.add_argument("--workload", default="uniform",
+                    choices=["uniform", "uneven", "adjoint", "seed"],
                     help="uniform: 100 x 9600 x 20 per mode (the default); uneven: the batched "
                          "form on 2000 events of log-normal size and mixed modes")
     ap.add_argument("--uneven-events", type=int, default=2000)
     ap.add_argument("--adjoint-tracks", type=int, default=100000)
+    ap.add_argument("--seed-tracks", type=int, default=1000000)
+    ap.add_argument("--seed-train-samples", type=int, default=4000000)
+    ap.add_argument("--seed-epochs", type=int, default=400)
     args = ap.parse_args()
     set_nevt(args.nevt)
     args.warmup = max(args.warmup, 3)
@@ -384,6 +546,9 @@ def main():
         return
     if args.workload == "adjoint":
         bench_adjoint(args, world, rank, local)
+        return
+    if args.workload == "seed":
+        bench_seed(args, world, rank, local)
         return
 
     import torch
