@@ -280,6 +280,24 @@ int fit_adjoint_backward(fit_handle* h, const fit_hits* hits, int nevt, const in
                          float* grad_hpos, float* grad_par0, float* grad_cov0, void* stream);
 
 /*
+ * fit_propagate_update_host: fit_propagate_update on HOST buffers (same
+ * structs, layouts and checks; every data pointer in in, out and hits is a
+ * host pointer, page-locked for the copies to overlap the kernels -- pageable
+ * memory works but serialises).  The library cuts the tracks into chunks of
+ * up to 131072 and moves each through one of two device staging sets on one
+ * of two internal streams: copy in, fit, copy out, so that one chunk's copies
+ * overlap the other's fit (the paper's transfers of Sec. 3.1 and its
+ * measurement with them included).  Asynchronous on `stream` like
+ * fit_propagate_update: the host buffers must stay valid and unchanged until
+ * the stream passes the call (fit_sync).  The staging (about 1 KiB per track
+ * of a chunk and per 20 layers, twice) is allocated on first use and kept by
+ * the handle.  Per-chunk results are bit-identical to fit_propagate_update.
+ */
+int fit_propagate_update_host(fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
+                              const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
+                              const int32_t* mode, void* stream);
+
+/*
  * Learned path-length seed for p2r.  The paper's p2r finds the path length to
  * the cylinder by discrete straight-line steps (Sec. 3.2); these entry points
  * add a small network, 8 -> 64 -> 64 -> 1 with ReLU, BF16 weights and FP32

@@ -167,6 +167,21 @@ int launch_segments(const fit_handle* h, FitArgs a, int nevt, const int64_t* ntr
   return FIT_OK;
 }
 
+// The fused fit of events [0, nevt) on the tracks of a (a.t0, a.t1 set per
+// run of same-mode events), on stream s.
+int run_fit(const fit_handle* h, const FitArgs& a, int nevt, const int64_t* ntrk,
+            const int32_t* mode, const char* who, cudaStream_t s) {
+  return launch_segments(h, a, nevt, ntrk, mode, who,
+                         [s, h](const FitArgs& a1, int m, unsigned nblk, int, int) {
+                           if (m == FIT_MODE_Z)
+                             fit_fused_kernel<FIT_MODE_Z><<<nblk, kBlock, 0, s>>>(a1);
+                           else if (h->seeded)
+                             launch_seeded_fit(a1, h->d_mlp, s);
+                           else
+                             fit_fused_kernel<FIT_MODE_R><<<nblk, kBlock, 0, s>>>(a1);
+                         });
+}
+
 // Scratch of fit_propagate_update_noalloc, in the library image instead of
 // allocated memory: per-event counters [FIT_NOALLOC_MAX_EVENTS][kEventSlots]
 // followed by the event offsets [FIT_NOALLOC_MAX_EVENTS + 1] (int64).  Every
@@ -245,17 +260,8 @@ int fit_propagate_update(fit_handle* h, const fit_tracks_in* in, const fit_track
   int rc = check_call(h, in, out, hits, nevt, ntrk, nlayer, mode, &total, "fit_propagate_update");
   if (rc != FIT_OK || total == 0) return rc;
   DeviceGuard g(h->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  rc = launch_segments(h, base_args(in, out, hits, nlayer, h->d_counters), nevt, ntrk, mode,
-                       "fit_propagate_update",
-                       [s, h](const FitArgs& a, int m, unsigned nblk, int, int) {
-                         if (m == FIT_MODE_Z)
-                           fit_fused_kernel<FIT_MODE_Z><<<nblk, kBlock, 0, s>>>(a);
-                         else if (h->seeded)
-                           launch_seeded_fit(a, h->d_mlp, s);
-                         else
-                           fit_fused_kernel<FIT_MODE_R><<<nblk, kBlock, 0, s>>>(a);
-                       });
+  rc = run_fit(h, base_args(in, out, hits, nlayer, h->d_counters), nevt, ntrk, mode,
+               "fit_propagate_update", static_cast<cudaStream_t>(stream));
   if (rc != FIT_OK) return rc;
   h->tracks += (uint64_t)total;
   return FIT_OK;
@@ -361,9 +367,10 @@ void fit_destroy(fit_handle* h) {
   if (!h) return;
   {
     DeviceGuard g(h->device);
-    if (h->d_counters || h->d_mlp) cudaDeviceSynchronize();
+    if (h->d_counters || h->d_mlp || h->host_stage) cudaDeviceSynchronize();
     if (h->d_counters) cudaFree(h->d_counters);
     if (h->d_mlp) cudaFree(h->d_mlp);
+    destroy_host_stage(h);
   }
   delete h;
 }

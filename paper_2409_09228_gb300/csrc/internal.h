@@ -80,6 +80,7 @@ struct fit_handle {
   uint64_t tracks = 0;
   void* d_mlp = nullptr;  // learned-seed weights (fit_mlp_attach), device
   bool seeded = false;    // p2r seeds from d_mlp
+  void* host_stage = nullptr;  // staging of fit_propagate_update_host (host.cu)
 };
 
 
@@ -95,5 +96,13 @@ FitArgs base_args(const fit_tracks_in* in, const fit_tracks_out* out, const fit_
 // The p2r fit seeded by the learned path length (mlp.cu), one track per
 // thread over a.t0 .. a.t1; img is the handle's d_mlp.
 void launch_seeded_fit(const FitArgs& a, const void* img, cudaStream_t s);
+
+// The fused fit of events [0, nevt) (fit.cu): one launch per run of
+// same-mode events, on stream s.
+int run_fit(const fit_handle* h, const FitArgs& a, int nevt, const int64_t* ntrk,
+            const int32_t* mode, const char* who, cudaStream_t s);
+
+// Frees the staging of fit_propagate_update_host (host.cu).
+void destroy_host_stage(fit_handle* h);
 
 }  // namespace fitimpl

@@ -88,7 +88,8 @@ EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_l
            "fit_plan_get_info", "fit_plan_destroy", "fit_tape_bytes", "fit_adjoint_forward",
            "fit_adjoint_backward", "fit_mlp_create", "fit_mlp_destroy", "fit_mlp_set_params",
            "fit_mlp_get_params", "fit_mlp_prepare", "fit_mlp_forward", "fit_mlp_gradient",
-           "fit_mlp_adam_step", "fit_mlp_train", "fit_mlp_attach", "fit_path_lengths")
+           "fit_mlp_adam_step", "fit_mlp_train", "fit_mlp_attach", "fit_path_lengths",
+           "fit_propagate_update_host")
 FIT_MLP_INPUTS = 8
 FIT_MLP_HIDDEN = 64
 FIT_MLP_PARAMS = 4801
@@ -158,6 +159,8 @@ def load(build_if_missing: bool = True):
                                        ctypes.POINTER(i64), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int32), vp, vp, vp, vp, vp, vp]
     L.fit_adjoint_backward.restype = ctypes.c_int
+    L.fit_propagate_update_host.argtypes = L.fit_propagate_update.argtypes
+    L.fit_propagate_update_host.restype = ctypes.c_int
     i32p = ctypes.POINTER(ctypes.c_int32)
     L.fit_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_uint64]
     L.fit_mlp_create.restype = ctypes.c_int
@@ -245,6 +248,39 @@ def fit_propagate_update(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Sequenc
     _check(L.fit_propagate_update(
         ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
         nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nlayer,
+        md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))
+
+
+def _hptr(a) -> Optional[int]:
+    """Address of a host array: a (pinned) torch CPU tensor or a numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda:
+            raise ValueError("fit_propagate_update_host takes host arrays")
+        return a.data_ptr()
+    return np.asarray(a).ctypes.data
+
+
+def fit_propagate_update_host(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Sequence[int],
+                              mode: Sequence[int], par_out=None, cov_out=None, q_out=None,
+                              chi2=None, chi2_layer=None, status=None, stream=None) -> None:
+    """The fused fit on HOST arrays (page-locked torch tensors for overlap, or
+    numpy arrays), copied through the library's device staging in chunks; the
+    arrays must stay alive until the stream passes the call (fit_sync)."""
+    L = load()
+    par_out = par_in if par_out is None else par_out
+    cov_out = cov_in if cov_out is None else cov_out
+    q_out = q_in if q_out is None else q_out
+    tin = fit_tracks_in(_hptr(par_in), _hptr(cov_in), _hptr(q_in), par_in.shape[-1])
+    tout = fit_tracks_out(_hptr(par_out), _hptr(cov_out), _hptr(q_out), _hptr(chi2),
+                          _hptr(chi2_layer), _hptr(status), par_out.shape[-1])
+    hits = fit_hits(_hptr(hpos), _hptr(hcov), hpos.shape[-1])
+    nt = np.ascontiguousarray(ntrk, dtype=np.int64)
+    md = np.ascontiguousarray(mode, dtype=np.int32)
+    _check(L.fit_propagate_update_host(
+        ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
+        nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), hpos.shape[0],
         md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))
 
 
