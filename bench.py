@@ -141,15 +141,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
-def dist_setup(gpus: int):
+def dist_setup(gpus: int, backend: str | None = None):
+    """Rank, world size and local rank from the torchrun environment; for
+    N > 1 one process group (NCCL on GPUs, gloo without).  Every rank fits its
+    own batch: there is no data exchange, only the barrier around the timed
+    region and the maximum of the ranks' times."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        import torch.distributed as dist
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -164,12 +172,15 @@ def max_over_ranks(world, x: float) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def workload(rank: int):
+    """The rank's own batch (weak scaling): both modes, NEVT x NTRK tracks,
+    drawn from seed SEED + 1000 rank."""
     from paper_2409_09228_gb300 import inputs
     n = NEVT * NTRK
     sets = [inputs.generate(m, n, seed=SEED + 1000 * rank, nlayer=NLAYER) for m in (0, 1)]
