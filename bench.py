@@ -377,6 +377,89 @@ def bench_adjoint(args, world, rank, local):
     print(json.dumps(line))
 
 
+FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal; no measured figure
+
+
+def bench_f64(args, world, rank, local):
+    """The FP64 variant on the bench workload (100 events x 9600 tracks x 20
+    layers per mode, double buffers, one launch per mode): what double costs
+    on GB300, whose FP64 rate is a small fraction of its FP32 rate."""
+    import torch
+    from paper_2409_09228_gb300 import fit
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sets = workload(rank)
+    # a double fit: the p2r iteration to 1e-12 R
+    f = fit.Fitter(fit.Geometry(sets[0].B, sets[0].surf, tol=1e-12),
+                   fit.Geometry(sets[1].B, sets[1].surf, tol=1e-12), device=local)
+    n = NEVT * NTRK
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(a.astype(np.float64) if a.dtype.kind == "f" else a)).to(dev)  # noqa: E731
+    d_in = [[up(a) for a in (s.par0, s.cov0, s.q, s.hpos, s.hcov)] for s in sets]
+    outs = [{"par": torch.empty((6, n), dtype=torch.float64, device=dev),
+             "cov": torch.empty((21, n), dtype=torch.float64, device=dev),
+             "q": torch.empty(n, dtype=torch.int32, device=dev),
+             "chi2": torch.empty(n, dtype=torch.float64, device=dev)} for _ in sets]
+    stream = torch.cuda.current_stream(dev)
+    ntrk = [NTRK] * NEVT
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(2)]
+    kern = [[], []]
+
+    def step(record=False):
+        for m in (0, 1):
+            if record:
+                ev[m][0].record(stream)
+            o = outs[m]
+            fit.fit_propagate_update_f64(f.h, *d_in[m], ntrk, [m] * NEVT, o["par"], o["cov"],
+                                         o["q"], o["chi2"], stream=stream)
+            if record:
+                ev[m][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    st = f.sync(stream)
+    assert st["nonfinite"] == 0 and st["no_intersection"] == 0, st
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+        torch.cuda.synchronize(dev)
+        for m in (0, 1):
+            kern[m].append(ev[m][0].elapsed_time(ev[m][1]))
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = max_over_ranks(world, sum(statistics.mean(k) for k in kern))
+    st = f.sync(stream)
+    f.close()
+    if rank != 0:
+        return
+    tl = n * NLAYER
+    kms = [statistics.mean(k) for k in kern]
+    ach = FLOPS_P2R * tl / (kms[0] / 1e3) / 1e12
+    line = {"metric": "track-layer propagate+update/s", "value": world * 2 * tl / (ms / 1e3),
+            "unit": "track-layer/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"FP64 variant: p2r + p2z, {NEVT} events x {NTRK} tracks x "
+                                   f"{NLAYER} layers per mode, double buffers, one launch per mode, "
+                                   f"p2r iteration to 1e-12 R",
+                       "inputs_exceed_l2": True},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS_NOMINAL,
+                         "unit": "TFLOP/s (FP64)", "frac": ach / FP64_PEAK_TFLOPS_NOMINAL,
+                         "peak_source": "nominal GB300 FP64 rate", "traffic": None,
+                         "kernel": "fit_f64_kernel<p2r>", "kernel_ms_p2r_p2z": kms,
+                         "flops_per_track_layer": FLOPS_P2R},
+            "clocks": clk, "gpu_launches": 2 * args.steps,
+            "p2r_iterations_per_track_layer": st["iterations"] / (args.steps * tl)}
+    print(json.dumps(line))
+
+
 def bench_seed(args, world, rank, local):
     """The learned p2r path-length seed.  Trains the network on 4M single p2r
     propagations labelled by the library's own exact iteration (run to
@@ -545,7 +628,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--nevt", type=int, default=NEVT, help="events per mode (default 100)")
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "uneven", "adjoint", "seed"],
+                    choices=["uniform", "uneven", "adjoint", "seed", "f64"],
                     help="uniform: 100 x 9600 x 20 per mode (the default); uneven: the batched "
                          "form on 2000 events of log-normal size and mixed modes")
     ap.add_argument("--uneven-events", type=int, default=2000)
@@ -568,6 +651,9 @@ def main():
         return
     if args.workload == "seed":
         bench_seed(args, world, rank, local)
+        return
+    if args.workload == "f64":
+        bench_f64(args, world, rank, local)
         return
 
     import torch

@@ -280,6 +280,45 @@ int fit_adjoint_backward(fit_handle* h, const fit_hits* hits, int nevt, const in
                          float* grad_hpos, float* grad_par0, float* grad_cov0, void* stream);
 
 /*
+ * FP64 variant.  The paper's test codes computed in double unless told
+ * otherwise (Sec. 5 runs p2r in FP32 only where double is emulated); this is
+ * the same fused fit with every floating-point operation in IEEE double, one
+ * track per thread, on double buffers of the same layouts (track index
+ * fastest, ld >= tracks; pointers 8-byte aligned).  Geometry, iteration limit
+ * and tolerance are the handle's; the field enters as kA * B in double.
+ * The p2r Jacobian is taken at the iteration's last iterate, one step (at most
+ * tol * R) short of the root, a relative error of ~kappa * tol * R: configure
+ * p2r with tol ~1e-12 for a double fit (the FP32 default 1e-6 limits it to
+ * ~1e-6).  Outputs, status bits and counters as fit_propagate_update.
+ */
+typedef struct {
+  const double* par;  /* [6][ld] */
+  const double* cov;  /* [21][ld] */
+  const int32_t* q;   /* [ld] */
+  int64_t ld;
+} fit_tracks_in_f64;
+
+typedef struct {
+  double* par;        /* [6][ld] */
+  double* cov;        /* [21][ld] */
+  int32_t* q;         /* [ld] */
+  double* chi2;       /* [ld] */
+  double* chi2_layer; /* [nlayer][ld] or NULL */
+  uint8_t* status;    /* [ld] or NULL */
+  int64_t ld;
+} fit_tracks_out_f64;
+
+typedef struct {
+  const double* pos;  /* [nlayer][3][ld] */
+  const double* cov;  /* [nlayer][6][ld] */
+  int64_t ld;
+} fit_hits_f64;
+
+int fit_propagate_update_f64(fit_handle* h, const fit_tracks_in_f64* in,
+                             const fit_tracks_out_f64* out, const fit_hits_f64* hits, int nevt,
+                             const int64_t* ntrk, int nlayer, const int32_t* mode, void* stream);
+
+/*
  * fit_propagate_update_host: fit_propagate_update on HOST buffers (same
  * structs, layouts and checks; every data pointer in in, out and hits is a
  * host pointer, page-locked for the copies to overlap the kernels -- pageable

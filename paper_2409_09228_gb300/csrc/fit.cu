@@ -77,6 +77,7 @@ int configure_modes(fit_handle* h, const fit_config* cfg_r, const fit_config* cf
     h->has[m] = true;
     h->nlayer[m] = c->nlayer;
     h->geo[m].kB = fitk::kA * c->B;
+    h->B[m] = c->B;
     h->geo[m].max_iter = c->max_iter > 0 ? c->max_iter : 10;
     h->geo[m].tol = c->tol > 0.f ? c->tol : 1e-6f;
   }

@@ -81,6 +81,7 @@ struct fit_handle {
   void* d_mlp = nullptr;  // learned-seed weights (fit_mlp_attach), device
   bool seeded = false;    // p2r seeds from d_mlp
   void* host_stage = nullptr;  // staging of fit_propagate_update_host (host.cu)
+  float B[2] = {0.f, 0.f};     // field of each mode's configuration
 };
 
 

@@ -1,5 +1,6 @@
-// Lane types for the fused kernel: float (one track per thread) and F2 (two
-// tracks per thread, held in the two halves of a float2).
+// Lane types for the fused kernel: float (one track per thread), F2 (two
+// tracks per thread, held in the two halves of a float2), and double (the
+// FP64 variant, one track per thread, IEEE operations throughout).
 //
 // The per-track math is written once as templates over the lane type.  With
 // F2 every add, multiply and fused multiply-add is one packed sm_100+
@@ -80,6 +81,19 @@ __device__ __forceinline__ F2 sel(M2 m, F2 a, F2 b) {
   return F2(m.x ? a.v.x : b.v.x, m.y ? a.v.y : b.v.y);
 }
 
+// ---- double (the FP64 variant, one track per thread): IEEE operations ------
+__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ double fsqrt(double x) { return x > 0.0 ? ::sqrt(x) : 0.0; }
+__device__ __forceinline__ double frsqrt(double x) { return 1.0 / ::sqrt(x); }
+__device__ __forceinline__ double fabs_(double x) { return ::fabs(x); }
+__device__ __forceinline__ double floor_(double x) { return ::floor(x); }
+__device__ __forceinline__ double copysign_(double a, double b) { return ::copysign(a, b); }
+__device__ __forceinline__ bool le(double a, double b) { return a <= b; }
+__device__ __forceinline__ bool lt(double a, double b) { return a < b; }
+__device__ __forceinline__ bool finite_(double a) { return isfinite(a); }
+__device__ __forceinline__ double sel(bool m, double a, double b) { return m ? a : b; }
+
 // ---- lanes ---------------------------------------------------------------
 template <class T>
 struct Lanes;
@@ -88,6 +102,13 @@ struct Lanes<float> {
   static constexpr int n = 1;
   using M = bool;
   __device__ __forceinline__ static float get(float a, int) { return a; }
+  __device__ __forceinline__ static bool get(bool m, int) { return m; }
+};
+template <>
+struct Lanes<double> {
+  static constexpr int n = 1;
+  using M = bool;
+  __device__ __forceinline__ static double get(double a, int) { return a; }
   __device__ __forceinline__ static bool get(bool m, int) { return m; }
 };
 template <>
@@ -104,6 +125,8 @@ __device__ __forceinline__ void ld(float& d, const float* p) { d = __ldcs(p); }
 __device__ __forceinline__ void ld(F2& d, const float* p) {
   d = F2(__ldcs(reinterpret_cast<const float2*>(p)));
 }
+__device__ __forceinline__ void ld(double& d, const double* p) { d = __ldcs(p); }
+__device__ __forceinline__ void st(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st(float* p, F2 v) { *reinterpret_cast<float2*>(p) = v.v; }
 

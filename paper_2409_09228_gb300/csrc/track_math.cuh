@@ -38,6 +38,20 @@ constexpr float kA = 0.00299792458f;  // GeV / (T cm)
 constexpr float kPi = 3.14159265358979f;
 constexpr float kTwoPi = 6.28318530717959f;
 
+// pi, 2 pi and 1/(2 pi) in the lane type's precision.
+template <class T>
+__device__ __forceinline__ T pi_() { return T(kPi); }
+template <>
+__device__ __forceinline__ double pi_<double>() { return 3.141592653589793; }
+template <class T>
+__device__ __forceinline__ T two_pi_() { return T(kTwoPi); }
+template <>
+__device__ __forceinline__ double two_pi_<double>() { return 6.283185307179586; }
+template <class T>
+__device__ __forceinline__ T inv_two_pi_() { return T(1.f / kTwoPi); }
+template <>
+__device__ __forceinline__ double inv_two_pi_<double>() { return 0.15915494309189535; }
+
 __host__ __device__ constexpr int sym(int i, int j) {
   return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i;
 }
@@ -150,6 +164,35 @@ __device__ __forceinline__ void turn_by(T& c, T& s, T d) {
   } else {
     sincos_cw(d, sd, cd);
   }
+  turn(c, s, cd, sd);
+}
+
+// FP64 variant: sin and cos from the CUDA math library; sin(u)/u and its
+// derivative by their Taylor series (to u^8 and u^7, remainders below 1e-19
+// relative for |u| < 1e-2) only where sin(u)/u and (cos u - sin(u)/u)/u
+// would cancel.
+__device__ __forceinline__ void sincos_cw(double x, double& s, double& c) { ::sincos(x, &s, &c); }
+__device__ __forceinline__ void sinc_c(double u, double& s, double& cu) {
+  double sn;
+  ::sincos(u, &sn, &cu);
+  if (::fabs(u) < 1e-2) {
+    const double u2 = u * u;
+    s = fma(u2, fma(u2, fma(u2, fma(u2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0),
+            1.0);
+  } else {
+    s = sn / u;
+  }
+}
+__device__ __forceinline__ double sinc_deriv(double u, double s, double cu) {
+  if (::fabs(u) < 1e-2) {
+    const double u2 = u * u;
+    return u * fma(u2, fma(u2, fma(u2, 1.0 / 45360.0, -1.0 / 840.0), 1.0 / 30.0), -1.0 / 3.0);
+  }
+  return (cu - s) / u;
+}
+__device__ __forceinline__ void turn_by(double& c, double& s, double d) {
+  double sd, cd;
+  ::sincos(d, &sd, &cd);
   turn(c, s, cd, sd);
 }
 
@@ -293,7 +336,7 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
   using M = typename Lanes<T>::M;
   const T sph = g.sphi, cph = g.cphi;
   const T x = p[0], y = p[1];
-  const T R2 = T(R * R);
+  const T R2 = T(R) * T(R);
   // The transverse circle (centre c, radius rho = 1/|kappa|) reaches radius
   // R only if |c| + rho >= R, which always holds when rho >= R.
   M fail = lt(T(1.f), T(R) * fabs_(kappa));
@@ -467,8 +510,8 @@ __device__ __forceinline__ typename Lanes<T>::M normalise(T (&p)[6], T (&c)[21],
                                                           Trig<T>& g, T phi_before, T th_before) {
   turn_by(g.cphi, g.sphi, p[4] - phi_before);
   turn_by(g.cth, g.sth, p[5] - th_before);
-  const T k = floor_((T(kPi) - p[4]) * T(1.f / kTwoPi));
-  p[4] = fma(k, T(kTwoPi), p[4]);
+  const T k = floor_((pi_<T>() - p[4]) * inv_two_pi_<T>());
+  p[4] = fma(k, two_pi_<T>(), p[4]);
   const auto flip = lt(p[3], T(0.f));
   if (any(flip)) {
     const T sgn = sel(flip, T(-1.f), T(1.f));

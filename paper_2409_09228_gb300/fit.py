@@ -89,7 +89,7 @@ EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_l
            "fit_adjoint_backward", "fit_mlp_create", "fit_mlp_destroy", "fit_mlp_set_params",
            "fit_mlp_get_params", "fit_mlp_prepare", "fit_mlp_forward", "fit_mlp_gradient",
            "fit_mlp_adam_step", "fit_mlp_train", "fit_mlp_attach", "fit_path_lengths",
-           "fit_propagate_update_host")
+           "fit_propagate_update_host", "fit_propagate_update_f64")
 FIT_MLP_INPUTS = 8
 FIT_MLP_HIDDEN = 64
 FIT_MLP_PARAMS = 4801
@@ -159,6 +159,8 @@ def load(build_if_missing: bool = True):
                                        ctypes.POINTER(i64), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int32), vp, vp, vp, vp, vp, vp]
     L.fit_adjoint_backward.restype = ctypes.c_int
+    L.fit_propagate_update_f64.argtypes = L.fit_propagate_update.argtypes
+    L.fit_propagate_update_f64.restype = ctypes.c_int
     L.fit_propagate_update_host.argtypes = L.fit_propagate_update.argtypes
     L.fit_propagate_update_host.restype = ctypes.c_int
     i32p = ctypes.POINTER(ctypes.c_int32)
@@ -248,6 +250,27 @@ def fit_propagate_update(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Sequenc
     _check(L.fit_propagate_update(
         ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
         nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nlayer,
+        md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))
+
+
+def fit_propagate_update_f64(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Sequence[int],
+                             mode: Sequence[int], par_out, cov_out, q_out, chi2,
+                             chi2_layer=None, status=None, stream=None) -> None:
+    """The FP64 variant of the fused fit on float64 CUDA tensors (same layouts)."""
+    import torch
+    for t in (par_in, cov_in, hpos, hcov, par_out, cov_out, chi2):
+        if t.dtype != torch.float64:
+            raise ValueError("fit_propagate_update_f64 takes float64 tensors")
+    L = load()
+    tin = fit_tracks_in(_ptr(par_in), _ptr(cov_in), _ptr(q_in), par_in.shape[-1])
+    tout = fit_tracks_out(_ptr(par_out), _ptr(cov_out), _ptr(q_out), _ptr(chi2),
+                          _ptr(chi2_layer), _ptr(status), par_out.shape[-1])
+    hits = fit_hits(_ptr(hpos), _ptr(hcov), hpos.shape[-1])
+    nt = np.ascontiguousarray(ntrk, dtype=np.int64)
+    md = np.ascontiguousarray(mode, dtype=np.int32)
+    _check(L.fit_propagate_update_f64(
+        ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
+        nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), hpos.shape[0],
         md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))
 
 

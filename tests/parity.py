@@ -43,31 +43,32 @@ def wrap(a):
     return (a + np.pi) % (2 * np.pi) - np.pi
 
 
-def scaled_errors(gpu: dict, ref: dict) -> dict:
+def scaled_errors(gpu: dict, ref: dict, rtol: float = RTOL, chi2_abs: float = CHI2_ABS) -> dict:
     """Per-track worst error of each output, in units of its tolerance (<= 1 passes)."""
     par_g, par_r = np.asarray(gpu["par"], np.float64), np.asarray(ref["par"], np.float64)
     d = par_g - par_r
     d[4] = wrap(d[4])
-    e_par = np.abs(d) / (RTOL * np.maximum(np.abs(par_r), PAR_FLOOR[:, None]))
+    e_par = np.abs(d) / (rtol * np.maximum(np.abs(par_r), PAR_FLOOR[:, None]))
     cov_g, cov_r = np.asarray(gpu["cov"], np.float64), np.asarray(ref["cov"], np.float64)
     dia = np.abs(cov_r[DIAG])
     dia[0] = dia[1] = dia[0] + dia[1]
     e_cov = np.empty_like(cov_r)
     for k, (i, j) in enumerate(PAIRS):
         scale = np.sqrt(dia[i] * dia[j])
-        e_cov[k] = np.abs(cov_g[k] - cov_r[k]) / (RTOL * np.maximum(scale, 1e-30))
+        e_cov[k] = np.abs(cov_g[k] - cov_r[k]) / (rtol * np.maximum(scale, 1e-30))
     c_g, c_r = np.asarray(gpu["chi2"], np.float64), np.asarray(ref["chi2"], np.float64)
-    e_chi2 = np.abs(c_g - c_r) / (RTOL * np.abs(c_r) + CHI2_ABS * np.sqrt(np.abs(c_r)) + 1e-30)
+    e_chi2 = np.abs(c_g - c_r) / (rtol * np.abs(c_r) + chi2_abs * np.sqrt(np.abs(c_r)) + 1e-30)
     return {"par": e_par.max(axis=0), "cov": e_cov.max(axis=0), "chi2": e_chi2,
             "par_each": e_par, "cov_each": e_cov}
 
 
-def check(gpu: dict, ref: dict, label: str = "") -> dict:
+def check(gpu: dict, ref: dict, label: str = "", rtol: float = RTOL,
+          chi2_abs: float = CHI2_ABS) -> dict:
     """Asserts parity on every track that neither side flagged; returns a summary."""
     st_g = np.asarray(gpu["status"]).astype(np.uint8)
     st_r = np.asarray(ref["status"]).astype(np.uint8)
     ok = (st_g == 0) & (st_r == 0)
-    e = scaled_errors(gpu, ref)
+    e = scaled_errors(gpu, ref, rtol, chi2_abs)
     worst = {k: float(e[k][ok].max()) if ok.any() else 0.0 for k in ("par", "cov", "chi2")}
     bad = ok & ((e["par"] > 1) | (e["cov"] > 1) | (e["chi2"] > 1))
     assert not bad.any(), (
