@@ -460,6 +460,66 @@ def bench_f64(args, world, rank, local):
     print(json.dumps(line))
 
 
+def bench_layout(args, world, rank, local):
+    """Ablation of the track and hit layout on the bench workload: structure
+    of arrays (the default path) against the paper's AoSoA with tiles of 32
+    tracks (fit_propagate_update_layout), same kernels otherwise."""
+    import torch
+    from paper_2409_09228_gb300 import fit, inputs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sets = workload(rank)
+    f = fit.Fitter(fit.Geometry(sets[0].B, sets[0].surf), fit.Geometry(sets[1].B, sets[1].surf),
+                   device=local)
+    n = NEVT * NTRK
+    ld = (n + 31) // 32 * 32
+    stream = torch.cuda.current_stream(dev)
+    ntrk = [NTRK] * NEVT
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    res = {}
+    for name, layout in (("soa", fit.FIT_LAYOUT_SOA), ("aosoa32", fit.FIT_LAYOUT_AOSOA32)):
+        conv = (lambda a: up(a)) if layout == fit.FIT_LAYOUT_SOA else \
+            (lambda a: up(inputs.to_aosoa32(a, ld)))
+        d = [[conv(a) for a in (s.par0, s.cov0)] + [up(np.pad(s.q, (0, ld - n)))] +
+             [conv(a) for a in (s.hpos, s.hcov)] for s in sets]
+        o = [{"par": torch.empty(6 * ld, device=dev), "cov": torch.empty(21 * ld, device=dev),
+              "q": torch.empty(ld, dtype=torch.int32, device=dev),
+              "chi2": torch.empty(ld, device=dev)} for _ in sets]
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(2)]
+        kern = [[], []]
+        for k in range(args.warmup + args.steps):
+            for m in (0, 1):
+                ev[m][0].record(stream)
+                fit.fit_propagate_update_layout(f.h, *d[m], ntrk, [m] * NEVT, layout, ld,
+                                                o[m]["par"], o[m]["cov"], o[m]["q"], o[m]["chi2"],
+                                                stream=stream)
+                ev[m][1].record(stream)
+            torch.cuda.synchronize(dev)
+            if k >= args.warmup:
+                for m in (0, 1):
+                    kern[m].append(ev[m][0].elapsed_time(ev[m][1]))
+        st = f.sync(stream)
+        assert st["nonfinite"] == 0 and st["no_intersection"] == 0, st
+        kms = [statistics.median(x) for x in kern]
+        res[name] = {"p2r_ms": kms[0], "p2z_ms": kms[1],
+                     "value": world * 2 * n * NLAYER / (sum(kms) / 1e3)}
+        del d, o
+    f.close()
+    if rank != 0:
+        return
+    ms = res["aosoa32"]["p2r_ms"] + res["aosoa32"]["p2z_ms"]
+    line = {"metric": "track-layer propagate+update/s", "value": res["aosoa32"]["value"],
+            "unit": "track-layer/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"layout ablation: p2r + p2z, {NEVT} events x {NTRK} tracks x "
+                                   f"{NLAYER} layers per mode, AoSoA tiles of 32 tracks against "
+                                   f"structure of arrays", "inputs_exceed_l2": True},
+            "layouts": res, "gpu_launches": 2 * (args.warmup + args.steps) * 2}
+    print(json.dumps(line))
+
+
 def bench_seed(args, world, rank, local):
     """The learned p2r path-length seed.  Trains the network on 4M single p2r
     propagations labelled by the library's own exact iteration (run to
@@ -628,7 +688,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--nevt", type=int, default=NEVT, help="events per mode (default 100)")
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "uneven", "adjoint", "seed", "f64"],
+                    choices=["uniform", "uneven", "adjoint", "seed", "f64", "layout"],
                     help="uniform: 100 x 9600 x 20 per mode (the default); uneven: the batched "
                          "form on 2000 events of log-normal size and mixed modes")
     ap.add_argument("--uneven-events", type=int, default=2000)
@@ -654,6 +714,9 @@ def main():
         return
     if args.workload == "f64":
         bench_f64(args, world, rank, local)
+        return
+    if args.workload == "layout":
+        bench_layout(args, world, rank, local)
         return
 
     import torch

@@ -280,6 +280,30 @@ int fit_adjoint_backward(fit_handle* h, const fit_hits* hits, int nevt, const in
                          float* grad_hpos, float* grad_par0, float* grad_cov0, void* stream);
 
 /*
+ * fit_propagate_update_layout: fit_propagate_update with the track and hit
+ * arrays in one of two layouts (paper Sec. 3.2 describes the test codes'
+ * Matriplex-style layout: tracks in blocks of bsize, each component of a
+ * block contiguous):
+ *   FIT_LAYOUT_SOA     structure of arrays, component k of track t at
+ *                      base[k * ld + t] (what every other entry point takes);
+ *   FIT_LAYOUT_AOSOA32 tiles of 32 consecutive tracks (of the events laid end
+ *                      to end): component k of track t at
+ *                      base[((t / 32) * K + k) * 32 + t % 32], K the number of
+ *                      components per track of that array (6 for par, 21 for
+ *                      cov, 3 nlayer for hit positions with k = 3 l + j,
+ *                      6 nlayer for hit covariances, nlayer for chi2_layer, 1
+ *                      for q, chi2 and status, which are then plain arrays).
+ *                      ld is the number of track slots, a multiple of 32.
+ * The arithmetic is the same; the results are bit-identical.  Not with the
+ * learned seed attached (FIT_ERR_ARG).
+ */
+#define FIT_LAYOUT_SOA 0
+#define FIT_LAYOUT_AOSOA32 1
+int fit_propagate_update_layout(fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
+                                const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
+                                const int32_t* mode, int layout, void* stream);
+
+/*
  * FP64 variant.  The paper's test codes computed in double unless told
  * otherwise (Sec. 5 runs p2r in FP32 only where double is emulated); this is
  * the same fused fit with every floating-point operation in IEEE double, one

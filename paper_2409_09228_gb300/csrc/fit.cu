@@ -29,12 +29,12 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 namespace {
 
-template <int MODE>
+template <int MODE, int L = 0>
 __global__ void __launch_bounds__(kBlock) fit_fused_kernel(const __grid_constant__ FitArgs a) {
   const int64_t t = pair_track(a);
   if (t >= a.t1) return;
   unsigned st[2] = {0u, 0u}, iters[2] = {0u, 0u};
-  run_pair<MODE>(a, a.geo, a.t0, a.t1, t, st, iters);
+  run_pair<MODE, L>(a, a.geo, a.t0, a.t1, t, st, iters);
   if (st[0]) count_status(st[0], a.counters);
   if (st[1]) count_status(st[1], a.counters);
   if (MODE == FIT_MODE_R) count_iterations(iters[0] + iters[1], &a.counters[4]);
@@ -263,6 +263,35 @@ int fit_propagate_update(fit_handle* h, const fit_tracks_in* in, const fit_track
   DeviceGuard g(h->device);
   rc = run_fit(h, base_args(in, out, hits, nlayer, h->d_counters), nevt, ntrk, mode,
                "fit_propagate_update", static_cast<cudaStream_t>(stream));
+  if (rc != FIT_OK) return rc;
+  h->tracks += (uint64_t)total;
+  return FIT_OK;
+}
+
+int fit_propagate_update_layout(fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
+                                const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
+                                const int32_t* mode, int layout, void* stream) {
+  static const char* kWho = "fit_propagate_update_layout";
+  g_last_error.clear();
+  if (!h) return fail(FIT_ERR_ARG, std::string(kWho) + ": NULL argument");
+  if (layout == FIT_LAYOUT_SOA)
+    return fit_propagate_update(h, in, out, hits, nevt, ntrk, nlayer, mode, stream);
+  if (layout != FIT_LAYOUT_AOSOA32) return fail(FIT_ERR_ARG, std::string(kWho) + ": unknown layout");
+  int64_t total = 0;
+  int rc = check_call(h, in, out, hits, nevt, ntrk, nlayer, mode, &total, kWho);
+  if (rc != FIT_OK || total == 0) return rc;
+  if ((in->ld | out->ld | hits->ld) & 31)
+    return fail(FIT_ERR_ARG, std::string(kWho) + ": AoSoA slots (ld) must be a multiple of 32");
+  if (h->seeded) return fail(FIT_ERR_ARG, std::string(kWho) + ": no learned seed in AoSoA");
+  DeviceGuard g(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = launch_segments(h, base_args(in, out, hits, nlayer, h->d_counters), nevt, ntrk, mode, kWho,
+                       [s](const FitArgs& a, int m, unsigned nblk, int, int) {
+                         if (m == FIT_MODE_Z)
+                           fit_fused_kernel<FIT_MODE_Z, 1><<<nblk, kBlock, 0, s>>>(a);
+                         else
+                           fit_fused_kernel<FIT_MODE_R, 1><<<nblk, kBlock, 0, s>>>(a);
+                       });
   if (rc != FIT_OK) return rc;
   h->tracks += (uint64_t)total;
   return FIT_OK;

@@ -34,24 +34,32 @@ struct State {
   fitk::Trig<T> g;
 };
 
-template <class T>
-__device__ __forceinline__ void load_state(const FitArgs& a, int64_t t, State<T>& s);
-template <>
+// Offset of component k (of K per track) of track t: structure of arrays
+// [K][ld] (layout 0), or tiles of 32 consecutive tracks [t / 32][K][32]
+// (layout 1, the paper's Matriplex-style AoSoA with bsize 32, Sec. 3.2).
+// Arrays with one component per track are the same in both.
+template <int L>
+__device__ __forceinline__ int64_t ix(int k, int64_t t, int64_t ld, int K) {
+  if (L == 0) return k * ld + t;
+  return (((t >> 5) * K + k) << 5) + (t & 31);
+}
+
+template <int L = 0>
 __device__ __forceinline__ void load_state(const FitArgs& a, int64_t t, State<float>& s) {
 #pragma unroll
-  for (int k = 0; k < 6; ++k) fitk::ld(s.p[k], a.par_in + k * a.ld_in + t);
+  for (int k = 0; k < 6; ++k) fitk::ld(s.p[k], a.par_in + ix<L>(k, t, a.ld_in, 6));
 #pragma unroll
-  for (int k = 0; k < 21; ++k) fitk::ld(s.c[k], a.cov_in + k * a.ld_in + t);
+  for (int k = 0; k < 21; ++k) fitk::ld(s.c[k], a.cov_in + ix<L>(k, t, a.ld_in, 21));
   s.qf = (float)__ldcs(a.q_in + t);
   s.chi2 = 0.f;
   s.g = fitk::trig_of(s.p);
 }
-template <>
+template <int L = 0>
 __device__ __forceinline__ void load_state(const FitArgs& a, int64_t t, State<F2>& s) {
 #pragma unroll
-  for (int k = 0; k < 6; ++k) fitk::ld(s.p[k], a.par_in + k * a.ld_in + t);
+  for (int k = 0; k < 6; ++k) fitk::ld(s.p[k], a.par_in + ix<L>(k, t, a.ld_in, 6));
 #pragma unroll
-  for (int k = 0; k < 21; ++k) fitk::ld(s.c[k], a.cov_in + k * a.ld_in + t);
+  for (int k = 0; k < 21; ++k) fitk::ld(s.c[k], a.cov_in + ix<L>(k, t, a.ld_in, 21));
   const int2 q = __ldcs(reinterpret_cast<const int2*>(a.q_in + t));
   s.qf = F2((float)q.x, (float)q.y);
   s.chi2 = F2(0.f);
@@ -74,7 +82,7 @@ __device__ __forceinline__ State<float> lane_of(const State<F2>& s, int i) {
 
 // Writes the outputs of the lanes of s (tracks t, t+1, ...), after the final
 // finiteness check.
-template <class T>
+template <int L = 0, class T>
 __device__ __forceinline__ void store_state(const FitArgs& a, int64_t t, const State<T>& s,
                                             unsigned (&st)[Lanes<T>::n]) {
   auto fin = fitk::finite_(s.chi2);
@@ -86,9 +94,9 @@ __device__ __forceinline__ void store_state(const FitArgs& a, int64_t t, const S
   for (int i = 0; i < Lanes<T>::n; ++i)
     if (!Lanes<T>::get(fin, i)) st[i] |= FIT_ST_NONFINITE;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) fitk::st(a.par_out + k * a.ld_out + t, s.p[k]);
+  for (int k = 0; k < 6; ++k) fitk::st(a.par_out + ix<L>(k, t, a.ld_out, 6), s.p[k]);
 #pragma unroll
-  for (int k = 0; k < 21; ++k) fitk::st(a.cov_out + k * a.ld_out + t, s.c[k]);
+  for (int k = 0; k < 21; ++k) fitk::st(a.cov_out + ix<L>(k, t, a.ld_out, 21), s.c[k]);
   fitk::st(a.chi2 + t, s.chi2);
 #pragma unroll
   for (int i = 0; i < Lanes<T>::n; ++i) {
@@ -103,7 +111,7 @@ __device__ __forceinline__ void store_state(const FitArgs& a, int64_t t, const S
 // surface some live lane cannot reach (its propagation is not applied), or
 // nlayer.  A lane whose update turns non-finite stops (alive false); its
 // later per-layer chi2 entries are 0.
-template <int MODE, class T>
+template <int MODE, class T, int L = 0>
 __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int64_t t, int l0,
                                           State<T>& s,
                                           unsigned (&st)[Lanes<T>::n],
@@ -116,9 +124,11 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
   for (int l = l0; l < a.nlayer; ++l) {
     T m[3], v[6];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) fitk::ld(m[k], hp + (3 * l + k) * ldh);
+    for (int k = 0; k < 3; ++k)
+      fitk::ld(m[k], L == 0 ? hp + (3 * l + k) * ldh : a.hpos + ix<L>(3 * l + k, t, ldh, 3 * a.nlayer));
 #pragma unroll
-    for (int k = 0; k < 6; ++k) fitk::ld(v[k], hc + (6 * l + k) * ldh);
+    for (int k = 0; k < 6; ++k)
+      fitk::ld(v[k], L == 0 ? hc + (6 * l + k) * ldh : a.hcov + ix<L>(6 * l + k, t, ldh, 6 * a.nlayer));
     const float sf = geo.surf.s[l];
     const T dkdw = s.qf * T(-geo.kB);
     M fail, nc = fitk::lt(T(1.f), T(0.f));
@@ -139,10 +149,11 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
     }
     x2 = fitk::sel(alive, x2, T(0.f));
     s.chi2 += x2;
-    if (a.chi2_layer) fitk::st(a.chi2_layer + (int64_t)l * a.ld_out + t, x2);
+    if (a.chi2_layer) fitk::st(a.chi2_layer + ix<L>(l, t, a.ld_out, a.nlayer), x2);
     if (!fitk::any(alive)) {
       if (a.chi2_layer)
-        for (int r = l + 1; r < a.nlayer; ++r) fitk::st(a.chi2_layer + (int64_t)r * a.ld_out + t, T(0.f));
+        for (int r = l + 1; r < a.nlayer; ++r)
+          fitk::st(a.chi2_layer + ix<L>(r, t, a.ld_out, a.nlayer), T(0.f));
       return a.nlayer;
     }
   }
@@ -151,20 +162,20 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
 
 // One track alone from layer l0 to the end (or to a surface it cannot
 // reach), then its outputs.
-template <int MODE>
+template <int MODE, int L = 0>
 __device__ __forceinline__ void finish_one(const FitArgs& a, const Geo& geo, int64_t t, int l0,
                                            State<float>& s, unsigned& st, unsigned& iters,
                                            bool alive) {
   unsigned st1[1] = {st}, it1[1] = {iters};
   if (alive) {
-    const int l = run_layers<MODE, float>(a, geo, t, l0, s, st1, it1, alive);
+    const int l = run_layers<MODE, float, L>(a, geo, t, l0, s, st1, it1, alive);
     if (l < a.nlayer) {
       st1[0] |= FIT_ST_NO_INTERSECTION;
       if (a.chi2_layer)
-        for (int r = l; r < a.nlayer; ++r) a.chi2_layer[(int64_t)r * a.ld_out + t] = 0.f;
+        for (int r = l; r < a.nlayer; ++r) a.chi2_layer[ix<L>(r, t, a.ld_out, a.nlayer)] = 0.f;
     }
   }
-  store_state(a, t, s, st1);
+  store_state<L>(a, t, s, st1);
   st = st1[0];
   iters = it1[0];
 }
@@ -173,29 +184,29 @@ __device__ __forceinline__ void finish_one(const FitArgs& a, const Geo& geo, int
 // shares packed instructions until a surface that one of them cannot reach,
 // from where each finishes alone.  One valid (the range starts or ends at an
 // odd index): that one alone.
-template <int MODE>
+template <int MODE, int L = 0>
 __device__ __forceinline__ void run_pair(const FitArgs& a, const Geo& geo, int64_t t0, int64_t t1,
                                          int64_t t, unsigned (&st)[2], unsigned (&iters)[2]) {
   const bool v0 = t >= t0, v1 = t + 1 < t1;
   if (v0 && v1) {
     State<F2> s;
-    load_state(a, t, s);
+    load_state<L>(a, t, s);
     fitk::M2 alive = {true, true};
-    const int l = run_layers<MODE, F2>(a, geo, t, 0, s, st, iters, alive);
+    const int l = run_layers<MODE, F2, L>(a, geo, t, 0, s, st, iters, alive);
     if (l == a.nlayer) {
-      store_state(a, t, s, st);
+      store_state<L>(a, t, s, st);
       return;
     }
 #pragma unroll 1
     for (int i = 0; i < 2; ++i) {
       State<float> one = lane_of(s, i);
-      finish_one<MODE>(a, geo, t + i, l, one, st[i], iters[i], Lanes<F2>::get(alive, i));
+      finish_one<MODE, L>(a, geo, t + i, l, one, st[i], iters[i], Lanes<F2>::get(alive, i));
     }
   } else {
     const int i = v0 ? 0 : 1;
     State<float> one;
-    load_state(a, t + i, one);
-    finish_one<MODE>(a, geo, t + i, 0, one, st[i], iters[i], true);
+    load_state<L>(a, t + i, one);
+    finish_one<MODE, L>(a, geo, t + i, 0, one, st[i], iters[i], true);
   }
 }
 

@@ -89,7 +89,10 @@ EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_l
            "fit_adjoint_backward", "fit_mlp_create", "fit_mlp_destroy", "fit_mlp_set_params",
            "fit_mlp_get_params", "fit_mlp_prepare", "fit_mlp_forward", "fit_mlp_gradient",
            "fit_mlp_adam_step", "fit_mlp_train", "fit_mlp_attach", "fit_path_lengths",
-           "fit_propagate_update_host", "fit_propagate_update_f64")
+           "fit_propagate_update_host", "fit_propagate_update_f64",
+           "fit_propagate_update_layout")
+FIT_LAYOUT_SOA = 0
+FIT_LAYOUT_AOSOA32 = 1
 FIT_MLP_INPUTS = 8
 FIT_MLP_HIDDEN = 64
 FIT_MLP_PARAMS = 4801
@@ -159,6 +162,8 @@ def load(build_if_missing: bool = True):
                                        ctypes.POINTER(i64), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int32), vp, vp, vp, vp, vp, vp]
     L.fit_adjoint_backward.restype = ctypes.c_int
+    L.fit_propagate_update_layout.argtypes = L.fit_propagate_update.argtypes[:-1] + [ctypes.c_int, vp]
+    L.fit_propagate_update_layout.restype = ctypes.c_int
     L.fit_propagate_update_f64.argtypes = L.fit_propagate_update.argtypes
     L.fit_propagate_update_f64.restype = ctypes.c_int
     L.fit_propagate_update_host.argtypes = L.fit_propagate_update.argtypes
@@ -251,6 +256,25 @@ def fit_propagate_update(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Sequenc
         ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
         nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nlayer,
         md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))
+
+
+def fit_propagate_update_layout(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Sequence[int],
+                                mode: Sequence[int], layout: int, ld: int, par_out, cov_out, q_out,
+                                chi2, chi2_layer=None, status=None, stream=None) -> None:
+    """The fused fit on arrays in `layout` (see fit.h); ld = track slots (for
+    FIT_LAYOUT_AOSOA32 a multiple of 32).  Tensors are passed by pointer."""
+    L = load()
+    tin = fit_tracks_in(_ptr(par_in), _ptr(cov_in), _ptr(q_in), ld)
+    tout = fit_tracks_out(_ptr(par_out), _ptr(cov_out), _ptr(q_out), _ptr(chi2),
+                          _ptr(chi2_layer), _ptr(status), ld)
+    hits = fit_hits(_ptr(hpos), _ptr(hcov), ld)
+    nt = np.ascontiguousarray(ntrk, dtype=np.int64)
+    md = np.ascontiguousarray(mode, dtype=np.int32)
+    nlayer = hpos.numel() // (3 * ld)
+    _check(L.fit_propagate_update_layout(
+        ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
+        nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nlayer,
+        md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(layout), _stream_handle(stream)))
 
 
 def fit_propagate_update_f64(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Sequence[int],

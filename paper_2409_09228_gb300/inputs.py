@@ -294,3 +294,23 @@ def generate_events(ntrk, modes, seed: int, nlayer: int = NLAYER, B: float = B_F
     cat = lambda name: np.concatenate([getattr(pools[0], name), getattr(pools[1], name)], axis=-1)[..., idx]  # noqa: E731
     return EventSet(ntrk, modes, pools[0].B, (pools[0].surf, pools[1].surf), cat("par0"),
                     cat("cov0"), cat("q"), cat("hpos"), cat("hcov"))
+
+
+# Layout of the arrays for fit_propagate_update_layout (FIT_LAYOUT_AOSOA32):
+# tiles of 32 consecutive tracks, each component of a tile contiguous.
+
+
+def to_aosoa32(a: np.ndarray, ld: int) -> np.ndarray:
+    """(K, n) or (nlayer, k, n) SoA -> flat AoSoA with tiles of 32 tracks over ld slots."""
+    a = np.asarray(a)
+    K = int(np.prod(a.shape[:-1]))
+    s = np.zeros((K, ld), a.dtype)
+    s[:, :a.shape[-1]] = a.reshape(K, -1)
+    return np.ascontiguousarray(s.reshape(K, ld // 32, 32).transpose(1, 0, 2)).reshape(-1)
+
+
+def from_aosoa32(a, shape, n: int) -> np.ndarray:
+    """Inverse of to_aosoa32 for arrays of `shape` (..., ld): returns (..., n)."""
+    a = np.asarray(a)
+    K, ld = int(np.prod(shape[:-1])), shape[-1]
+    return a.reshape(ld // 32, K, 32).transpose(1, 0, 2).reshape(shape)[..., :n]
