@@ -520,6 +520,69 @@ def bench_layout(args, world, rank, local):
     print(json.dumps(line))
 
 
+def bench_find(args, world, rank, local):
+    """Track finding: NEVT/4 events x 9600 tracks x 20 layers per mode, 4
+    candidate hits per layer (the track's own with probability 0.95, noise
+    displaced by 20 hit errors), chi2 gate 30, FP32, one launch per mode."""
+    import torch
+    from paper_2409_09228_gb300 import fit, inputs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nevt, ncand = max(1, NEVT // 4), 4
+    n = nevt * NTRK
+    sets = [inputs.generate(m, n, seed=SEED + 1000 * rank, nlayer=NLAYER) for m in (0, 1)]
+    cands = [inputs.generate_candidates(s, ncand, seed=SEED + 1000 * rank, spread=20.0) for s in sets]
+    f = fit.Fitter(fit.Geometry(sets[0].B, sets[0].surf), fit.Geometry(sets[1].B, sets[1].surf),
+                   device=local)
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d = [[up(a) for a in (s.par0, s.cov0, s.q, c.cpos, c.ccov)] for s, c in zip(sets, cands)]
+    for s, c in zip(sets, cands):
+        del s.hpos, s.hcov, c.cpos, c.ccov
+    o = [[torch.empty((6, n), device=dev), torch.empty((21, n), device=dev),
+          torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, device=dev)] for _ in sets]
+    chosen = [torch.empty((NLAYER, n), dtype=torch.int8, device=dev) for _ in sets]
+    stream = torch.cuda.current_stream(dev)
+    ntrk = [NTRK] * nevt
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(2)]
+    kern = [[], []]
+    for k in range(args.warmup + args.steps):
+        for m in (0, 1):
+            ev[m][0].record(stream)
+            fit.fit_find_tracks(f.h, *d[m], ntrk, [m] * nevt, 30.0, chosen[m], *o[m],
+                                stream=stream)
+            ev[m][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if k >= args.warmup:
+            for m in (0, 1):
+                kern[m].append(ev[m][0].elapsed_time(ev[m][1]))
+    st = f.sync(stream)
+    taken = float((chosen[0] >= 0).float().mean().item())
+    f.close()
+    kms = [statistics.median(x) for x in kern]
+    ms = max_over_ranks(world, sum(kms))
+    if rank != 0:
+        return
+    tl = n * NLAYER
+    peaks = load_peaks()
+    bpl = 36.0 * ncand + 1.0 + (BYTES_TRACK_IN + BYTES_TRACK_OUT - 1) / NLAYER
+    ach = bpl * tl / (kms[0] / 1e3) / 1e9
+    line = {"metric": "track-layer propagate+find+update/s", "value": world * 2 * tl / (ms / 1e3),
+            "unit": "track-layer/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"track finding: p2r + p2z, {nevt} events x {NTRK} tracks x "
+                                   f"{NLAYER} layers per mode, {ncand} candidate hits per layer, "
+                                   f"chi2 gate 30", "inputs_exceed_l2": True},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": "fit_find_kernel<p2r, float>", "bytes_per_track_layer": bpl,
+                         "kernel_ms_p2r_p2z": kms},
+            "gpu_launches": 2 * (args.warmup + args.steps), "p2r_layers_with_a_hit": taken,
+            "status": st}
+    print(json.dumps(line))
+
+
 def bench_seed(args, world, rank, local):
     """The learned p2r path-length seed.  Trains the network on 4M single p2r
     propagations labelled by the library's own exact iteration (run to
@@ -688,7 +751,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--nevt", type=int, default=NEVT, help="events per mode (default 100)")
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "uneven", "adjoint", "seed", "f64", "layout"],
+                    choices=["uniform", "uneven", "adjoint", "seed", "f64", "layout", "find"],
                     help="uniform: 100 x 9600 x 20 per mode (the default); uneven: the batched "
                          "form on 2000 events of log-normal size and mixed modes")
     ap.add_argument("--uneven-events", type=int, default=2000)
@@ -717,6 +780,9 @@ def main():
         return
     if args.workload == "layout":
         bench_layout(args, world, rank, local)
+        return
+    if args.workload == "find":
+        bench_find(args, world, rank, local)
         return
 
     import torch

@@ -343,6 +343,43 @@ int fit_propagate_update_f64(fit_handle* h, const fit_tracks_in_f64* in,
                              const int64_t* ntrk, int nlayer, const int32_t* mode, void* stream);
 
 /*
+ * Track finding.  The paper's test codes take the one hit given on each layer;
+ * the pattern recognition around them (mkFit, Sec. 3) chooses it among
+ * several.  fit_find_tracks does that choice inside the fused fit: on each
+ * layer the track is propagated, every candidate hit is tried against the
+ * prediction (chi2 = r^T S^-1 r of the update it would make), and the
+ * candidate with the smallest chi2 strictly below chi2_gate (the lowest
+ * index among equal chi2) updates the track; if none qualifies the track keeps
+ * its prediction and the layer adds nothing to chi2.  chosen [nlayer][ld_out]
+ * (DEVICE int8) receives the candidate taken on each layer, or -1 (also for
+ * layers a stopped track did not reach).  Candidates: positions
+ * [nlayer][ncand][3][ld] and covariances [nlayer][ncand][6][ld], track
+ * fastest, 1 <= ncand <= 16.  One track per thread; outputs, status bits and
+ * counters as fit_propagate_update.  fit_find_tracks_f64: the same in double.
+ */
+typedef struct {
+  const float* pos;
+  const float* cov;
+  int32_t ncand;
+  int64_t ld;
+} fit_candidates;
+
+typedef struct {
+  const double* pos;
+  const double* cov;
+  int32_t ncand;
+  int64_t ld;
+} fit_candidates_f64;
+
+int fit_find_tracks(fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
+                    const fit_candidates* cand, float chi2_gate, int8_t* chosen, int nevt,
+                    const int64_t* ntrk, int nlayer, const int32_t* mode, void* stream);
+int fit_find_tracks_f64(fit_handle* h, const fit_tracks_in_f64* in, const fit_tracks_out_f64* out,
+                        const fit_candidates_f64* cand, double chi2_gate, int8_t* chosen,
+                        int nevt, const int64_t* ntrk, int nlayer, const int32_t* mode,
+                        void* stream);
+
+/*
  * fit_propagate_update_host: fit_propagate_update on HOST buffers (same
  * structs, layouts and checks; every data pointer in in, out and hits is a
  * host pointer, page-locked for the copies to overlap the kernels -- pageable

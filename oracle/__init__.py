@@ -82,6 +82,9 @@ class Oracle:
         L.orc_update.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D, _I, _D]
         L.orc_fit.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, ctypes.c_int64,
                               _D, _D, _I, _D, _D, _D, _D, _I, _D, _D, _U8, ctypes.c_int]
+        L.orc_find.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, ctypes.c_int64, _D,
+                               _D, _I, ctypes.c_int, _D, _D, ctypes.c_double, _D, _D, _I, _D, _D,
+                               _I, _D, _U8, ctypes.c_int]
         L.orc_path_lengths.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64, _D, _I, _D,
                                        _D, _U8, ctypes.c_int]
         L.orc_chi2_grad.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _D,
@@ -160,6 +163,28 @@ class Oracle:
         return self.fit(ts.mode, ts.B, ts.surf, ts.par0, ts.cov0, ts.q, ts.hpos, ts.hcov,
                         nthreads=nthreads, want_layers=want_layers)
 
+    def find(self, mode: int, B: float, surf, par0, cov0, q0, cpos, ccov, gate: float,
+             nthreads: int = 0) -> dict:
+        """Track finding: per layer the candidate (cpos (nlayer, ncand, 3, n), ccov
+        (nlayer, ncand, 6, n)) with the smallest chi2 below the gate updates the
+        track, or none; returns the fit outputs, chosen (nlayer, n) (-1 = none)
+        and the chi2 of every candidate tried (nlayer, ncand, n)."""
+        surf = _d(surf)
+        par0, cov0, cpos, ccov = _d(par0), _d(cov0), _d(cpos), _d(ccov)
+        q0 = np.ascontiguousarray(q0, dtype=np.int32)
+        nlayer, ncand, _, n = cpos.shape
+        par, cov = np.zeros((6, n)), np.zeros((21, n))
+        q, chi2 = np.zeros(n, np.int32), np.zeros(n)
+        cl = np.zeros((nlayer, n))
+        chosen = np.zeros((nlayer, n), np.int32)
+        cc = np.zeros((nlayer, ncand, n))
+        status = np.zeros(n, np.uint8)
+        self.L.orc_find(mode, B, nlayer, _p(surf), n, _p(par0), _p(cov0), _p(q0, _I), ncand,
+                        _p(cpos), _p(ccov), float(gate), _p(par), _p(cov), _p(q, _I), _p(chi2),
+                        _p(cl), _p(chosen, _I), _p(cc), _p(status, _U8), nthreads)
+        return {"par": par, "cov": cov, "q": q, "chi2": chi2, "chi2_layer": cl,
+                "chosen": chosen, "cand_chi2": cc, "status": status}
+
     def chi2_grad(self, mode: int, B: float, surf, par0, cov0, q0, hpos, hcov,
                   nthreads: int = 0) -> dict:
         """Gradient of each track's summed chi2 w.r.t. its initial parameters and hits."""
@@ -220,6 +245,10 @@ def fit_set(*a, **k):
 
 def chi2_grad(*a, **k):
     return default().chi2_grad(*a, **k)
+
+
+def find(*a, **k):
+    return default().find(*a, **k)
 
 
 def unpack_sym6(c21) -> np.ndarray:

@@ -359,6 +359,60 @@ unsigned fit_track(int mode, double B, int nlayer, const double* surf, Track<T>&
   return st;
 }
 
+// Track finding (paper Sec. 3: the tracks come from mkFit's pattern
+// recognition, whose choice of hit per layer the test codes leave out; they
+// take the one hit given).  On each layer the track is propagated and each of
+// ncand candidate hits is tried with the Kalman update above on a copy of the
+// prediction; the candidate with the smallest chi2 strictly below the gate
+// (the lowest index among equal chi2) updates the track, or none does and the
+// track keeps its prediction.  cpos/ccov: [nlayer * ncand] candidates, layer
+// major; chosen[l] = the candidate taken on layer l or -1; cand_chi2
+// [nlayer * ncand] receives every tried chi2 (NaN for layers not reached).
+template <class T>
+unsigned find_track(int mode, double B, int nlayer, const double* surf, Track<T>& t, int ncand,
+                    const T (*cpos)[3], const T (*ccov)[3][3], double gate, T* chi2_layer,
+                    int* chosen, T* cand_chi2, T& chi2) {
+  unsigned st = 0u;
+  chi2 = 0.0;
+  for (int l = 0; l < nlayer; ++l) {
+    chi2_layer[l] = 0.0;
+    chosen[l] = -1;
+    for (int k = 0; k < ncand; ++k) cand_chi2[l * ncand + k] = std::nan("");
+  }
+  for (int l = 0; l < nlayer; ++l) {
+    Track<T> keep = t;
+    unsigned s = propagate(mode, t, B, surf[l]);
+    if (s) {
+      st |= s;
+      t = keep;
+      break;
+    }
+    int best = -1;
+    double best_chi2 = gate;
+    for (int k = 0; k < ncand; ++k) {
+      Track<T> trial = t;
+      unsigned ignored = 0u;
+      T c = kalman_update(mode, trial, cpos[l * ncand + k], ccov[l * ncand + k], ignored);
+      cand_chi2[l * ncand + k] = c;
+      if (value(c) < best_chi2) {
+        best = k;
+        best_chi2 = value(c);
+      }
+    }
+    chosen[l] = best;
+    if (best < 0) continue;
+    T c = kalman_update(mode, t, cpos[l * ncand + best], ccov[l * ncand + best], st);
+    if (!all_finite(t) || !std::isfinite(value(c))) {
+      st |= ST_NONFINITE;
+      t = keep;
+      break;
+    }
+    chi2_layer[l] = c;
+    chi2 = chi2 + c;
+  }
+  return st;
+}
+
 template <class F>
 void parallel_for(int64_t n, int nthreads, F f) {
   if (nthreads <= 0) nthreads = (int)std::max(1u, std::thread::hardware_concurrency());
@@ -500,6 +554,49 @@ int orc_fit(int mode, double B, int nlayer, const double* surf, int64_t n,
     chi2[i] = c2;
     if (chi2_layer)
       for (int l = 0; l < nlayer; ++l) chi2_layer[l * n + i] = cl[l];
+    status[i] = (unsigned char)st;
+  });
+  return 0;
+}
+
+// Track finding over n tracks (find_track).  Candidates [nlayer][ncand][3][n]
+// and [nlayer][ncand][6][n]; chosen [nlayer][n]; cand_chi2 [nlayer][ncand][n]
+// (may be NULL); other layouts as orc_fit.
+int orc_find(int mode, double B, int nlayer, const double* surf, int64_t n, const double* par0,
+             const double* cov0, const int* q0, int ncand, const double* cpos,
+             const double* ccov, double gate, double* par, double* cov, int* q, double* chi2,
+             double* chi2_layer, int* chosen, double* cand_chi2, unsigned char* status,
+             int nthreads) {
+  parallel_for(n, nthreads, [&](int64_t i) {
+    Track<double> t;
+    for (int k = 0; k < 6; ++k) t.p[k] = par0[k * n + i];
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 6; ++b) t.C[a][b] = cov0[packed_index(a, b) * n + i];
+    t.q = q0[i];
+    const int nc = nlayer * ncand;
+    std::vector<double> m(3 * nc), V(9 * nc), cl(nlayer), cc(nc);
+    std::vector<int> ch(nlayer);
+    for (int j = 0; j < nc; ++j) {
+      for (int k = 0; k < 3; ++k) m[3 * j + k] = cpos[(3 * j + k) * n + i];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) V[9 * j + 3 * a + b] = ccov[(6 * j + packed_index(a, b)) * n + i];
+    }
+    double c2 = 0.0;
+    unsigned st = find_track(mode, B, nlayer, surf, t, ncand,
+                             reinterpret_cast<const double(*)[3]>(m.data()),
+                             reinterpret_cast<const double(*)[3][3]>(V.data()), gate, cl.data(),
+                             ch.data(), cc.data(), c2);
+    for (int k = 0; k < 6; ++k) par[k * n + i] = t.p[k];
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b <= a; ++b) cov[packed_index(a, b) * n + i] = t.C[a][b];
+    q[i] = t.q;
+    chi2[i] = c2;
+    for (int l = 0; l < nlayer; ++l) {
+      if (chi2_layer) chi2_layer[l * n + i] = cl[l];
+      chosen[l * n + i] = ch[l];
+    }
+    if (cand_chi2)
+      for (int j = 0; j < nc; ++j) cand_chi2[j * n + i] = cc[j];
     status[i] = (unsigned char)st;
   });
   return 0;

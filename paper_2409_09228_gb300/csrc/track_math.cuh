@@ -559,4 +559,37 @@ __device__ __forceinline__ T update_r(T (&p)[6], T (&c)[21], const T (&m)[3], co
   return kalman_2d<false>(p, c, a, b, S00, S01, S11, r0, r1);
 }
 
+// chi2 = r^T S^-1 r of a hit against the prediction, without the update
+// (track finding tries every candidate).  The same expressions as
+// update_z / update_r and kalman_2d, so the chi2 of the chosen candidate is
+// the one its update returns.
+template <class T>
+__device__ __forceinline__ T chi2_z(const T (&p)[6], const T (&c)[21], const T (&m)[3],
+                                    const T (&v)[6]) {
+  const T S00 = c[sym(0, 0)] + v[0], S01 = c[sym(1, 0)] + v[1], S11 = c[sym(1, 1)] + v[2];
+  const T r0 = m[0] - p[0], r1 = m[1] - p[1];
+  const T w01 = S01 * S01;
+  const T det = fma(S00, S11, -w01) - fma(S01, S01, -w01);
+  const T id = fdiv(T(1.f), det);
+  return fma(S11 * r0, r0, fma(S00 * r1, r1, T(-2.f) * S01 * r0 * r1)) * id;
+}
+template <class T>
+__device__ __forceinline__ T chi2_r(const T (&p)[6], const T (&c)[21], const T (&m)[3],
+                                    const T (&v)[6]) {
+  const T ir = frsqrt(fma(m[0], m[0], m[1] * m[1]));
+  const T sh = m[1] * ir, ch = m[0] * ir;
+  const T a0 = fma(ch, c[sym(0, 1)], -(sh * c[sym(0, 0)]));
+  const T a1 = fma(ch, c[sym(1, 1)], -(sh * c[sym(1, 0)]));
+  const T a2 = fma(ch, c[sym(2, 1)], -(sh * c[sym(2, 0)]));
+  const T vtt = fma(sh * sh, v[0], fma(ch * ch, v[2], T(-2.f) * sh * ch * v[1]));
+  const T vtz = fma(ch, v[4], -(sh * v[3]));
+  const T S00 = fma(ch, a1, -(sh * a0)) + vtt;
+  const T S01 = a2 + vtz;
+  const T S11 = c[sym(2, 2)] + v[5];
+  const T r0 = fma(ch, m[1] - p[1], -(sh * (m[0] - p[0])));
+  const T r1 = m[2] - p[2];
+  const T id = fdiv(T(1.f), fma(S00, S11, -(S01 * S01)));
+  return fma(S11 * r0, r0, fma(S00 * r1, r1, T(-2.f) * S01 * r0 * r1)) * id;
+}
+
 }  // namespace fitk

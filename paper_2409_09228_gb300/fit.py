@@ -77,6 +77,11 @@ class fit_plan_info(ctypes.Structure):
                 ("items", ctypes.c_int32), ("tuned", ctypes.c_int32), ("best_ms", ctypes.c_float)]
 
 
+class fit_candidates(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("ncand", ctypes.c_int32),
+                ("ld", ctypes.c_int64)]
+
+
 class fit_mlp_train_config(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
                 ("lr_final", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
@@ -90,7 +95,7 @@ EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_l
            "fit_mlp_get_params", "fit_mlp_prepare", "fit_mlp_forward", "fit_mlp_gradient",
            "fit_mlp_adam_step", "fit_mlp_train", "fit_mlp_attach", "fit_path_lengths",
            "fit_propagate_update_host", "fit_propagate_update_f64",
-           "fit_propagate_update_layout")
+           "fit_propagate_update_layout", "fit_find_tracks", "fit_find_tracks_f64")
 FIT_LAYOUT_SOA = 0
 FIT_LAYOUT_AOSOA32 = 1
 FIT_MLP_INPUTS = 8
@@ -162,6 +167,16 @@ def load(build_if_missing: bool = True):
                                        ctypes.POINTER(i64), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int32), vp, vp, vp, vp, vp, vp]
     L.fit_adjoint_backward.restype = ctypes.c_int
+    L.fit_find_tracks.argtypes = [vp, ctypes.POINTER(fit_tracks_in), ctypes.POINTER(fit_tracks_out),
+                                  ctypes.POINTER(fit_candidates), ctypes.c_float, vp, ctypes.c_int,
+                                  ctypes.POINTER(i64), ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                  vp]
+    L.fit_find_tracks.restype = ctypes.c_int
+    L.fit_find_tracks_f64.argtypes = [vp, ctypes.POINTER(fit_tracks_in),
+                                      ctypes.POINTER(fit_tracks_out), ctypes.POINTER(fit_candidates),
+                                      ctypes.c_double, vp, ctypes.c_int, ctypes.POINTER(i64),
+                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int32), vp]
+    L.fit_find_tracks_f64.restype = ctypes.c_int
     L.fit_propagate_update_layout.argtypes = L.fit_propagate_update.argtypes[:-1] + [ctypes.c_int, vp]
     L.fit_propagate_update_layout.restype = ctypes.c_int
     L.fit_propagate_update_f64.argtypes = L.fit_propagate_update.argtypes
@@ -296,6 +311,39 @@ def fit_propagate_update_f64(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Seq
         ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
         nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), hpos.shape[0],
         md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))
+
+
+def fit_find_tracks(h: int, par_in, cov_in, q_in, cpos, ccov, ntrk: Sequence[int],
+                    mode: Sequence[int], chi2_gate: float, chosen, par_out, cov_out, q_out, chi2,
+                    chi2_layer=None, status=None, stream=None) -> None:
+    """Track finding on CUDA tensors: cpos (nlayer, ncand, 3, ld), ccov
+    (nlayer, ncand, 6, ld), chosen (nlayer, ld) int8; float32 tensors call the
+    FP32 kernels, float64 tensors the FP64 ones."""
+    import torch
+    f64 = par_in.dtype == torch.float64
+    L = load()
+    tin = fit_tracks_in(_ptr(par_in), _ptr(cov_in), _ptr(q_in), par_in.shape[-1])
+    tout = fit_tracks_out(_ptr(par_out), _ptr(cov_out), _ptr(q_out), _ptr(chi2),
+                          _ptr(chi2_layer), _ptr(status), par_out.shape[-1])
+    cand = fit_candidates(_ptr(cpos), _ptr(ccov), cpos.shape[1], cpos.shape[-1])
+    nt = np.ascontiguousarray(ntrk, dtype=np.int64)
+    md = np.ascontiguousarray(mode, dtype=np.int32)
+    fn = L.fit_find_tracks_f64 if f64 else L.fit_find_tracks
+    _check(fn(ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(cand),
+              float(chi2_gate), _ptr(chosen), len(nt),
+              nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cpos.shape[0],
+              md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))
+
+
+def fit_find_tracks_f64(h: int, par_in, cov_in, q_in, cpos, ccov, ntrk, mode, chi2_gate, chosen,
+                        par_out, cov_out, q_out, chi2, chi2_layer=None, status=None,
+                        stream=None) -> None:
+    """fit_find_tracks on float64 tensors (the FP64 kernels)."""
+    import torch
+    if par_in.dtype != torch.float64:
+        raise ValueError("fit_find_tracks_f64 takes float64 tensors")
+    fit_find_tracks(h, par_in, cov_in, q_in, cpos, ccov, ntrk, mode, chi2_gate, chosen, par_out,
+                    cov_out, q_out, chi2, chi2_layer, status, stream)
 
 
 def _hptr(a) -> Optional[int]:

@@ -296,6 +296,62 @@ def generate_events(ntrk, modes, seed: int, nlayer: int = NLAYER, B: float = B_F
                     cat("cov0"), cat("q"), cat("hpos"), cat("hcov"))
 
 
+@dataclass
+class CandidateSet:
+    """Candidate hits for track finding: positions (nlayer, ncand, 3, n) and
+    covariances (nlayer, ncand, 6, n), float32; true_slot (nlayer, n) is the
+    slot holding the track's own hit, or -1 where it is missing."""
+    cpos: np.ndarray
+    ccov: np.ndarray
+    true_slot: np.ndarray
+
+
+def generate_candidates(ts: TrackSet, ncand: int, seed: int, p_true: float = 0.95,
+                        spread: float = 5.0) -> CandidateSet:
+    """ncand candidate hits per track and layer: the track's own hit (from ts)
+    with probability p_true in a random slot, the other slots noise hits on
+    the same surface, displaced from the track's hit by `spread` times the hit
+    errors (sigma_rphi along the azimuthal direction, sigma_2 along z for
+    cylinders or along the radius for planes), each with the covariance a hit
+    at its place would have."""
+    nlayer, _, n = ts.hpos.shape
+    g = _rng(seed, 19)
+    present = g.random((nlayer, n)) < p_true
+    slot = g.integers(0, ncand, (nlayer, n))
+    true_slot = np.where(present, slot, -1).astype(np.int32)
+    cpos = np.empty((nlayer, ncand, 3, n), np.float32)
+    ccov = np.zeros((nlayer, ncand, 6, n), np.float32)
+    a, b = SIGMA_RPHI ** 2, SIGMA_2 ** 2
+    for l in range(nlayer):
+        hx, hy, hz = (ts.hpos[l, k].astype(np.float64) for k in range(3))
+        r = np.hypot(hx, hy)
+        phi = np.arctan2(hy, hx)
+        for k in range(ncand):
+            n1 = g.standard_normal(n) * spread
+            n2 = g.standard_normal(n) * spread
+            if ts.mode == MODE_R:
+                ph = phi + n1 * SIGMA_RPHI / r
+                c, sn = np.cos(ph), np.sin(ph)
+                pos = (r * c, r * sn, hz + n2 * SIGMA_2)
+                cov = (a * sn * sn, -a * sn * c, a * c * c, 0.0 * c, 0.0 * c, np.full(n, b))
+            else:
+                ux, uy = hx / r, hy / r
+                x = hx + n1 * SIGMA_RPHI * -uy + n2 * SIGMA_2 * ux
+                y = hy + n1 * SIGMA_RPHI * ux + n2 * SIGMA_2 * uy
+                rr = np.hypot(x, y)
+                vx, vy = x / rr, y / rr
+                tx, ty = -vy, vx
+                pos = (x, y, hz)
+                cov = (a * tx * tx + b * vx * vx, a * ty * tx + b * vy * vx,
+                       a * ty * ty + b * vy * vy, 0.0 * x, 0.0 * x, 0.0 * x)
+            mine = true_slot[l] == k
+            for j in range(3):
+                cpos[l, k, j] = np.where(mine, ts.hpos[l, j], pos[j])
+            for j in range(6):
+                ccov[l, k, j] = np.where(mine, ts.hcov[l, j], cov[j])
+    return CandidateSet(cpos, ccov, true_slot)
+
+
 # Layout of the arrays for fit_propagate_update_layout (FIT_LAYOUT_AOSOA32):
 # tiles of 32 consecutive tracks, each component of a tile contiguous.
 
