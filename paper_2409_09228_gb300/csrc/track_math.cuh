@@ -383,7 +383,8 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
     const T b = fma(px, c1, py * s1);
     const T c2 = fma(px, px, fma(py, py, -R2));
     const T disc = fma(b, b, -c2);
-    d = sel(le(T(0.f), disc), fdiv(-c2, b + copysign_(fsqrt(disc), b)), fdiv(-c2, T(2.f) * b));
+    // where the line misses the circle (disc < 0) the Newton step -c2 / (2 b)
+    d = fdiv(-c2, sel(le(T(0.f), disc), b + copysign_(fsqrt(disc), b), T(2.f) * b));
     d = sel(conv, T(0.f), d);
     h += d;
     conv = or_(conv, le(fabs_(d), T(tol_abs)));
