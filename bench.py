@@ -905,7 +905,7 @@ def main():
             "e2e": {"value": world * units_per_step / (e2e_ms / 1e3), "unit": "track-layer/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "path": "fit_propagate_update_host on page-locked host buffers (chunked "
-                            "copies in, fit, copies out, two streams)"},
+                            "copies in, fit, copies out, three streams)"},
             "gpu_launches": 2 * args.steps, "p2r_iterations_per_track_layer": it_per}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sets)

@@ -384,14 +384,14 @@ int fit_find_tracks_f64(fit_handle* h, const fit_tracks_in_f64* in, const fit_tr
  * structs, layouts and checks; every data pointer in in, out and hits is a
  * host pointer, page-locked for the copies to overlap the kernels -- pageable
  * memory works but serialises).  The library cuts the tracks into chunks of
- * up to 131072 and moves each through one of two device staging sets on one
- * of two internal streams: copy in, fit, copy out, so that one chunk's copies
- * overlap the other's fit (the paper's transfers of Sec. 3.1 and its
+ * up to 131072 and moves each through one of three device staging sets on
+ * one of three internal streams: copy in, fit, copy out, so that one chunk's
+ * copies overlap the others' fits (the paper's transfers of Sec. 3.1 and its
  * measurement with them included).  Asynchronous on `stream` like
  * fit_propagate_update: the host buffers must stay valid and unchanged until
  * the stream passes the call (fit_sync).  The staging (about 1 KiB per track
- * of a chunk and per 20 layers, twice) is allocated on first use and kept by
- * the handle.  Per-chunk results are bit-identical to fit_propagate_update.
+ * of a chunk and per 20 layers, three times) is allocated on first use and
+ * kept by the handle.  Per-chunk results are bit-identical to fit_propagate_update.
  */
 int fit_propagate_update_host(fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
                               const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,

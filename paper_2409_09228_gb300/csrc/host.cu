@@ -1,9 +1,10 @@
 // fit_propagate_update_host: the fused fit on HOST buffers.  The tracks are
 // cut into chunks of at most kChunk; chunk i goes through device staging set
-// i % 2 on internal stream i % 2 -- host-to-device copies, the fused kernels,
-// device-to-host copies -- so the copies of one chunk overlap the fit of the
-// other (paper Sec. 3.1: inputs are copied to the device before the kernel and
-// results back after it).  The caller's stream orders the whole call.
+// i % kSets on internal stream i % kSets -- host-to-device copies, the fused
+// kernels, device-to-host copies -- so the copies of one chunk overlap the fit
+// and copies of the others (paper Sec. 3.1: inputs are copied to the device
+// before the kernel and results back after it).  The caller's stream orders
+// the whole call.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,13 +20,17 @@ using namespace fitimpl;
 namespace {
 
 constexpr int64_t kChunk = 131072;  // tracks per chunk (a multiple of 4)
+// Staging sets and streams.  On GB300 (one H2D copy engine at ~211 GB/s),
+// 131072 tracks and 3 sets measured best end to end: 9.3 ms per bench step
+// against 9.6 with 2 sets and 12-14 ms with 65536 or 262144 tracks.
+constexpr int kSets = 3;
 
 struct HostStage {
   int64_t cap = 0;  // tracks per staging set
   int nlayer = 0;
-  char* buf[2] = {nullptr, nullptr};
-  cudaStream_t st[2] = {nullptr, nullptr};
-  cudaEvent_t ev_start = nullptr, ev_done[2] = {nullptr, nullptr};
+  char* buf[kSets] = {};
+  cudaStream_t st[kSets] = {};
+  cudaEvent_t ev_start = nullptr, ev_done[kSets] = {};
 };
 
 // Staging set layout: par [6][cap], cov [21][cap], q [cap], chi2 [cap],
@@ -57,7 +62,7 @@ Set carve(char* b, int64_t cap, int nlayer) {
 }
 
 void free_stage(HostStage* hs) {
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kSets; ++i) {
     if (hs->buf[i]) cudaFree(hs->buf[i]);
     if (hs->st[i]) cudaStreamDestroy(hs->st[i]);
     if (hs->ev_done[i]) cudaEventDestroy(hs->ev_done[i]);
@@ -82,7 +87,7 @@ int stage_for(fit_handle* h, int64_t cap, int nlayer, HostStage** out) {
   hs->cap = cap;
   hs->nlayer = nlayer;
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+  for (int i = 0; i < kSets && e == cudaSuccess; ++i) {
     e = cudaMalloc(&hs->buf[i], set_bytes(cap, nlayer));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hs->st[i], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hs->ev_done[i], cudaEventDisableTiming);
@@ -133,7 +138,8 @@ extern "C" int fit_propagate_update_host(fit_handle* h, const fit_tracks_in* in,
   if (rc != FIT_OK) return rc;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaEventRecord(hs->ev_start, cs);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(hs->st[i], hs->ev_start, 0);
+  for (int i = 0; i < kSets && e == cudaSuccess; ++i)
+    e = cudaStreamWaitEvent(hs->st[i], hs->ev_start, 0);
   if (e != cudaSuccess) return cuda_fail(e, "fit_propagate_update_host: stream order");
 
   const size_t P = (size_t)hs->cap * 4;  // staging pitch
@@ -146,7 +152,7 @@ extern "C" int fit_propagate_update_host(fit_handle* h, const fit_tracks_in* in,
   int k = 0;
   for (int64_t c0 = 0; c0 < total; c0 += hs->cap, ++k) {
     const int64_t c1 = std::min(total, c0 + hs->cap), nc = c1 - c0;
-    const int b = k & 1;
+    const int b = k % kSets;
     cudaStream_t s = hs->st[b];
     const Set S = carve(hs->buf[b], hs->cap, hs->nlayer);
     // the events (or parts of events) of [c0, c1), in order
@@ -187,7 +193,7 @@ extern "C" int fit_propagate_update_host(fit_handle* h, const fit_tracks_in* in,
                     cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "fit_propagate_update_host: copy to host");
   }
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+  for (int i = 0; i < kSets && e == cudaSuccess; ++i) {
     e = cudaEventRecord(hs->ev_done[i], hs->st[i]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, hs->ev_done[i], 0);
   }

@@ -1,5 +1,5 @@
 """fit_propagate_update_host: the fused fit on host buffers, copied through
-the library's two staging sets in chunks of 131072 tracks.  Its results must
+the library's three staging sets in chunks of 131072 tracks.  Its results must
 be bit-identical to fit_propagate_update on the same data in device memory:
 chunks start at even track indices, so every track meets the same kernel with
 the same pairing."""
