@@ -480,8 +480,8 @@ int fit_mlp_adam_step(fit_mlp* m, const float* grad, float lr, void* stream);
  * fit_mlp_train: minimises the mean squared error of the network's output
  * against the targets by Adam over `epochs` passes of batches of cfg->batch
  * consecutive samples (from a per-epoch offset drawn from cfg->seed; n must
- * be >= cfg->batch).  Each step is one forward+backward kernel and one Adam
- * kernel on `stream`.  loss_per_epoch (HOST [epochs], may be NULL) receives the
+ * be >= cfg->batch).  Each step is one forward+backward kernel, one Adam
+ * kernel and one kernel that rebuilds the BF16 weights, on `stream`.  loss_per_epoch (HOST [epochs], may be NULL) receives the
  * mean training loss of each epoch; the call then waits for the stream.
  */
 int fit_mlp_train(fit_mlp* m, const float* x, const float* target, int64_t n,

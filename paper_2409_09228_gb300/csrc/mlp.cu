@@ -390,14 +390,19 @@ __global__ void __launch_bounds__(256)
 
 // One Adam step (Kingma and Ba, 2015, Algorithm 1) with the gradient grad, or
 // the sum of nblk partials when grad is NULL; bc1 = 1 - beta1^t and
-// bc2 = 1 - beta2^t.  Adds curve_scale times the partials' squared errors to
-// *curve, then rebuilds the BF16 image from the new parameters.
-__global__ void __launch_bounds__(1024)
+// bc2 = 1 - beta2^t; one parameter per thread over the grid.  Block 0 adds
+// curve_scale times the partials' squared errors to *curve.  The BF16 image
+// is rebuilt from the new parameters by mlp_image_kernel afterwards.
+constexpr int kAdamThreads = 256;
+constexpr int kAdamBlocks = (mlpk::kParams + kAdamThreads - 1) / kAdamThreads;
+
+__global__ void __launch_bounds__(kAdamThreads)
     mlp_adam_kernel(float* __restrict__ P, float* __restrict__ M, float* __restrict__ V,
                     const float* __restrict__ grad, const float* __restrict__ partials, int nblk,
                     float lr, float beta1, float beta2, float eps, float bc1, float bc2,
-                    TrainImage* img, float* curve, float curve_scale) {
-  for (int i = threadIdx.x; i < mlpk::kParams; i += blockDim.x) {
+                    float* curve, float curve_scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < mlpk::kParams) {
     float gi;
     if (grad) {
       gi = grad[i];
@@ -411,13 +416,11 @@ __global__ void __launch_bounds__(1024)
     V[i] = v;
     P[i] -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
   }
-  if (curve && threadIdx.x == 0) {
+  if (curve && i == 0) {
     float s = 0.f;
     for (int b = 0; b < nblk; ++b) s += partials[(int64_t)b * kPartial + kSse];
     *curve += s * curve_scale;
   }
-  __syncthreads();
-  build_image(P, img, threadIdx.x, blockDim.x);
 }
 
 // ---- the p2r path-length iteration alone ---------------------------------------
@@ -581,9 +584,10 @@ int launch_adam(fit_mlp* m, const float* grad, int nblk, float lr, float* curve,
   m->step += 1;
   const double bc1 = 1.0 - std::pow((double)m->beta1, (double)m->step);
   const double bc2 = 1.0 - std::pow((double)m->beta2, (double)m->step);
-  mlp_adam_kernel<<<1, 1024, 0, s>>>(m->d_params, m->d_m, m->d_v, grad, m->d_partials, nblk, lr,
-                                     m->beta1, m->beta2, m->eps, (float)bc1, (float)bc2, m->d_img,
-                                     curve, scale);
+  mlp_adam_kernel<<<kAdamBlocks, kAdamThreads, 0, s>>>(m->d_params, m->d_m, m->d_v, grad,
+                                                        m->d_partials, nblk, lr, m->beta1, m->beta2,
+                                                        m->eps, (float)bc1, (float)bc2, curve, scale);
+  mlp_image_kernel<<<1, 1024, 0, s>>>(m->d_params, m->d_img);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FIT_OK : cuda_fail(e, "fit_mlp: Adam launch");
 }
