@@ -68,9 +68,10 @@ def fp32_peak_tflops(mhz: float) -> float:
     return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
-# The sources fit_fused_kernel is compiled from; the DRAM traffic committed
-# under profiles/ holds only while they hash to the value recorded there.
-FUSED_SOURCES = ("include/fit.h", "paper_2409_09228_gb300/csrc/fit.cu",
+# The sources fit_fused_kernel is compiled from (and the constants it takes
+# from include/fit.h); the DRAM traffic committed under profiles/ holds only
+# while they hash to the value recorded there.
+FUSED_SOURCES = ("paper_2409_09228_gb300/csrc/fit.cu",
                  "paper_2409_09228_gb300/csrc/fused.cuh",
                  "paper_2409_09228_gb300/csrc/track_math.cuh",
                  "paper_2409_09228_gb300/csrc/lanes.cuh",
@@ -82,6 +83,8 @@ def kernel_source_hash() -> str:
     for name in FUSED_SOURCES:
         with open(os.path.join(ROOT, name), "rb") as f:
             h.update(name.encode() + f.read())
+    with open(os.path.join(ROOT, "include", "fit.h")) as f:
+        h.update("".join(l for l in f if l.startswith("#define FIT_")).encode())
     return h.hexdigest()[:16]
 
 
