@@ -138,6 +138,23 @@ def test_f32_finder_unique_choices_agree(mode):
         f.close()
 
 
+def test_f64_finder_with_the_most_candidates():
+    """ncand = 16, the limit: the FP64 kernel still takes exactly the oracle's
+    choices."""
+    ts = inputs.generate(inputs.MODE_Z, 257, seed=61)
+    cs = inputs.generate_candidates(ts, 16, seed=61, spread=10.0, p_true=0.9)
+    f = fit.Fitter(None, fit.Geometry(ts.B, ts.surf, tol=1e-12))
+    try:
+        ref = oracle.find(1, ts.B, ts.surf, ts.par0, ts.cov0, ts.q, cs.cpos, cs.ccov, GATE)
+        got, _ = _find(f, ts, cs, np.float64)
+        ok = (got["status"] == 0) & (ref["status"] == 0)
+        assert ok.mean() > 0.99
+        assert np.array_equal(got["chosen"][:, ok], ref["chosen"][:, ok])
+        assert got["chosen"].max() > 8  # the high slots are used
+    finally:
+        f.close()
+
+
 def test_one_candidate_is_the_fit():
     ts = inputs.generate(inputs.MODE_R, 1000, seed=51)
     f = fit.Fitter(fit.Geometry(ts.B, ts.surf), None)

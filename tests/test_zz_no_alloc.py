@@ -100,3 +100,39 @@ def test_noalloc_rejects_too_many_events():
                                          chi2=t(ld))
     assert e.value.code == fit.FIT_ERR_ARG
     assert "FIT_NOALLOC_MAX_EVENTS" in str(e.value)
+
+
+def test_noalloc_at_the_event_limit():
+    """FIT_NOALLOC_MAX_EVENTS events (the limit) of one track each, modes
+    alternating in runs: every event's counters are its own track's."""
+    nevt = fit.FIT_NOALLOC_MAX_EVENTS
+    modes = (np.arange(nevt) // 7) % 2
+    sets = [inputs.generate(inputs.MODE_R, int((modes == 0).sum()), seed=511),
+            inputs.generate(inputs.MODE_Z, int((modes == 1).sum()), seed=512)]
+    order = np.argsort(np.argsort(modes, kind="stable"), kind="stable")  # rank within the sorted pools
+    pools = gpu_util.concat(sets)
+    c = {k: v[..., order] for k, v in pools.items()}
+    ld = gpu_util.pad_ld(nevt)
+    dev_in = [gpu_util.to_dev(c[k], ld) for k in ("par0", "cov0", "q", "hpos", "hcov")]
+    geom_r = fit.Geometry(sets[0].B, inputs.surfaces(inputs.MODE_R))
+    geom_z = fit.Geometry(sets[0].B, inputs.surfaces(inputs.MODE_Z))
+    out = {"par": torch.empty((6, ld), device="cuda"), "cov": torch.empty((21, ld), device="cuda"),
+           "q": torch.empty(ld, dtype=torch.int32, device="cuda"),
+           "chi2": torch.empty(ld, device="cuda"),
+           "status": torch.empty(ld, dtype=torch.uint8, device="cuda")}
+    per_event = fit.fit_propagate_update_noalloc(
+        geom_r, geom_z, *dev_in, [1] * nevt, modes.tolist(), par_out=out["par"],
+        cov_out=out["cov"], q_out=out["q"], chi2=out["chi2"], status=out["status"])
+    assert len(per_event) == nevt
+    assert all(p["tracks"] == 1 for p in per_event)
+    st = out["status"].cpu().numpy()[:nevt]
+    assert (st == 0).all() and all(p["no_intersection"] == 0 for p in per_event)
+    it = np.array([p["iterations"] for p in per_event])
+    assert (it[modes == 1] == 0).all() and (it[modes == 0] >= 20).all()
+    # and the fit agrees with the handle path on the same tracks
+    f = fit.Fitter(geom_r, geom_z)
+    ref = f.run(*dev_in, [1] * nevt, modes.tolist())
+    f.close()
+    got = {k: v.cpu().numpy()[..., :nevt] for k, v in out.items()}
+    parity.check(got, {k: v.cpu().numpy()[..., :nevt] for k, v in ref.items() if v is not None},
+                 "no-alloc at the event limit")
