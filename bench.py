@@ -866,22 +866,24 @@ def main():
                  "hbm_frac": hbm_ach / peaks["hbm_gbs"], "alu_frac": alu_ach / alu_peak,
                  "kernel_ms_p2r_p2z": kernel_ms})
 
-    # End to end through the C ABI on host buffers: fit_propagate_update_host
-    # copies each mode's tracks and hits from page-locked host memory through
-    # the library's staging, fits them and copies the results back, per step.
-    pinned_in = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-                  for a in (s.par0, s.cov0, s.q, s.hpos, s.hcov)] for s in sets]
-    pinned_out = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
-                   for k, v in o.items() if v is not None} for o in outs]
-    h2d = sum(t.numel() * t.element_size() for p in pinned_in for t in p)
-    d2h = sum(t.numel() * t.element_size() for p in pinned_out for t in p.values())
+    # End to end through the C ABI on host buffers: one fit_propagate_update_host
+    # call per step copies both modes' tracks and hits (the p2r events, then the
+    # p2z events, in one page-locked array set) through the library's staging,
+    # fits them and copies the results back.
+    pinned_in = [torch.from_numpy(np.ascontiguousarray(
+        np.concatenate([getattr(s, k) for s in sets], axis=-1))).pin_memory()
+        for k in ("par0", "cov0", "q", "hpos", "hcov")]
+    pinned_out = {k: torch.empty(v.shape[:-1] + (2 * n,), dtype=v.dtype).pin_memory()
+                  for k, v in outs[0].items() if v is not None}
+    h2d = sum(t.numel() * t.element_size() for t in pinned_in)
+    d2h = sum(t.numel() * t.element_size() for t in pinned_out.values())
+    ntrk_both, mode_both = ntrk * 2, [0] * NEVT + [1] * NEVT
 
     def e2e_step():
-        for m in (0, 1):
-            o = pinned_out[m]
-            fit.fit_propagate_update_host(f.h, *pinned_in[m], ntrk, [m] * NEVT, par_out=o["par"],
-                                          cov_out=o["cov"], q_out=o["q"], chi2=o["chi2"],
-                                          status=o["status"], stream=stream)
+        o = pinned_out
+        fit.fit_propagate_update_host(f.h, *pinned_in, ntrk_both, mode_both, par_out=o["par"],
+                                      cov_out=o["cov"], q_out=o["q"], chi2=o["chi2"],
+                                      status=o["status"], stream=stream)
 
     e2e_ms = float("nan")
     if args.e2e_steps > 0:
@@ -907,8 +909,9 @@ def main():
             "config": config_dict(args), "roofline": roof, "clocks": clk,
             "e2e": {"value": world * units_per_step / (e2e_ms / 1e3), "unit": "track-layer/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "path": "fit_propagate_update_host on page-locked host buffers (chunked "
-                            "copies in, fit, copies out, three streams)"},
+                    "path": "one fit_propagate_update_host call per step on page-locked host "
+                            "buffers holding both modes (chunked copies in, fit, copies out, "
+                            "three streams)"},
             "gpu_launches": 2 * args.steps, "p2r_iterations_per_track_layer": it_per}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sets)
