@@ -149,3 +149,28 @@ def test_autograd_function():
     assert np.allclose(par0.grad.cpu().numpy()[:, :ts.n], g_p, rtol=1e-6, atol=1e-5)
     assert cov0.grad is not None and torch.isfinite(cov0.grad[:, :ts.n]).all()
     f.close()
+
+
+def test_full_size_adjoint_sampled():
+    """The adjoint's workload at its full size (100k p2r tracks x 20 layers,
+    seed 5, ld = n as in the benchmark): gradients against the oracle's on
+    sampled tracks."""
+    n = 100_000
+    ts = inputs.generate(inputs.MODE_R, n, seed=5)
+    ld = gpu_util.pad_ld(n)
+    d = [gpu_util.to_dev(a, ld) for a in (ts.par0, ts.cov0, ts.q, ts.hpos, ts.hcov)]
+    f = fit.Fitter(fit.Geometry(ts.B, ts.surf), None)
+    try:
+        out, g_h, g_p = _gpu_grad(f, ts, ld, d)
+        assert (out["status"].cpu().numpy()[:n] == 0).all()
+        idx = np.sort(np.random.default_rng(3).choice(n, 400, replace=False))
+        sub = ts.subset(idx)
+        ref = oracle.chi2_grad(sub.mode, sub.B, sub.surf, sub.par0, sub.cov0, sub.q, sub.hpos,
+                               sub.hcov)
+        assert (ref["status"] == 0).all()
+        gh, gp = g_h[..., idx], g_p[:, idx]
+        scale = np.maximum(np.abs(ref["g_hpos"]).max(axis=(0, 1)), np.abs(ref["g_par0"]).max(axis=0))
+        _assert_close(gh, ref["g_hpos"], scale[None, None, :], "full-size hit gradient")
+        _assert_close(gp, ref["g_par0"], scale[None, :], "full-size initial-parameter gradient")
+    finally:
+        f.close()

@@ -156,3 +156,38 @@ def test_plan_argument_errors():
             fit.fit_plan_create(f.h, [10], [0], 20, threads_per_block=96)
     finally:
         f.close()
+
+
+def test_full_size_uneven_batch_sampled():
+    """The uneven-batch workload at its full size (2000 events, log-normal
+    track counts, mixed modes, seed 3: ~6.5M tracks), run by a plan in the
+    launch shape the benchmark times: the oracle on sampled tracks of both
+    modes, properties on all."""
+    nt = inputs.uneven_event_sizes(2000, 3)
+    md = inputs.uneven_event_modes(2000, 3)
+    ev = inputs.generate_events(nt, md, seed=3)
+    n = ev.n
+    ld, dev_in = _device(ev)
+    f = fit.Fitter(*_geoms(ev))
+    plan = fit.fit_plan_create(f.h, nt, md, 20)
+    try:
+        out = f.outputs(n, ld=ld)
+        fit.fit_plan_run(plan, *dev_in, par_out=out["par"], cov_out=out["cov"], q_out=out["q"],
+                         chi2=out["chi2"], status=out["status"])
+        st = f.sync()
+        assert st["tracks"] == n and st["no_intersection"] == 0 and st["nonfinite"] == 0
+        got = _fetch(out, n)
+        assert (got["status"] == 0).all() and np.isfinite(got["par"]).all()
+        assert abs(got["chi2"].mean() / 20 - 2.0) < 0.02
+        mode_of_track = np.repeat(md, nt)
+        rng = np.random.default_rng(1)
+        for m in (0, 1):
+            pool = np.nonzero(mode_of_track == m)[0]
+            idx = np.sort(rng.choice(pool, 1500, replace=False))
+            sub = inputs.TrackSet(m, ev.B, ev.surf[m], ev.par0[:, idx], ev.cov0[:, idx], ev.q[idx],
+                                  ev.hpos[:, :, idx], ev.hcov[:, :, idx])
+            parity.check({k: v[..., idx] for k, v in got.items()}, oracle.fit_set(sub),
+                         f"full-size uneven batch, mode {m}")
+    finally:
+        fit.fit_plan_destroy(plan)
+        f.close()

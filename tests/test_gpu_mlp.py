@@ -346,3 +346,28 @@ def test_argument_errors():
             fit.fit_mlp_set_params(m, np.zeros(10))
     finally:
         fit.fit_mlp_destroy(m)
+
+
+def test_full_size_seeded_fit_sampled(trained):
+    """The learned seed's workload at its full size (1M p2r tracks x 20
+    layers, seed 4): the seeded fit against the oracle on sampled tracks."""
+    m, _ = trained
+    n = 1_000_000
+    ts = inputs.generate(inputs.MODE_R, n, seed=4)
+    ld = gpu_util.pad_ld(n)
+    d = [gpu_util.to_dev(a, ld) for a in (ts.par0, ts.cov0, ts.q, ts.hpos, ts.hcov)]
+    f = fit.Fitter(_geom(), None)
+    try:
+        fit.fit_mlp_attach(f.h, m)
+        out = f.run(*d, [n], [0])
+        st = f.sync()
+        assert st["tracks"] == n and st["no_intersection"] == 0 and st["nonfinite"] == 0
+        assert st["not_converged"] == 0 and st["iterations"] < 1.2 * n * 20
+        got = {k: v.cpu().numpy()[..., :n] for k, v in out.items() if v is not None}
+        assert (got["status"] == 0).all()
+        idx = np.unique(np.concatenate([[0, n - 1],
+                                        np.random.default_rng(2).choice(n, 3000, replace=False)]))
+        parity.check({k: v[..., idx] for k, v in got.items()}, oracle.fit_set(ts.subset(idx)),
+                     "full-size seeded fit")
+    finally:
+        f.close()
