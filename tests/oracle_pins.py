@@ -13,7 +13,10 @@ when the oracle disagrees with something the physics or mathematics fixes:
   (C^-1 + H^T V^-1 H)^-1; the chi2 split into filtered residual and state
   change; C - C+ positive semi-definite;
 * the whole filter on generated tracks: chi2 per layer ~ chi2(2) and pulls
-  ~ N(0, 1) (the generator's noise model is the filter's measurement model).
+  ~ N(0, 1) (the generator's noise model is the filter's measurement model);
+* track finding: the composition of the pinned single steps with the argmin
+  over candidates written out here; one candidate without a gate is the plain
+  fit; nothing under the gate is pure propagation.
 
 tests/test_oracle.py runs every pin on the oracle; tests/test_oracle_mutants.py
 plants mistakes in copies of oracle.cpp and checks that some pin fails.
@@ -453,6 +456,87 @@ def pin_chi2_gradient_fd(orc):
                 assert np.allclose(g["g_hpos"][l, k], fd, rtol=1e-4, atol=1e-3), (l, k, g["g_hpos"][l, k], fd)
 
 
+# ---- track finding (orc_find) ----------------------------------------------------
+
+
+def _find_layerwise(orc, ts, cs, gate):
+    """Track finding composed here from the single-step propagate and update,
+    with the argmin over candidates written out."""
+    nlayer, ncand, _, n = cs.cpos.shape
+    out = {"par": np.zeros((6, n)), "cov": np.zeros((21, n)), "chi2": np.zeros(n),
+           "chosen": np.full((nlayer, n), -1)}
+    for i in range(n):
+        p, c, q = ts.par0[:, i].astype(np.float64), ts.cov0[:, i].astype(np.float64), int(ts.q[i])
+        chi2 = 0.0
+        for l in range(nlayer):
+            st, pp, cp = orc.propagate(ts.mode, ts.B, float(ts.surf[l]), q, p, c)
+            if st:
+                break
+            trial = [orc.update(ts.mode, q, pp, cp, cs.cpos[l, k, :, i], cs.ccov[l, k, :, i])[4]
+                     for k in range(ncand)]
+            ok = [k for k in range(ncand) if trial[k] < gate]
+            p, c = pp, cp
+            if ok:
+                best = min(ok, key=lambda k: (trial[k], k))
+                out["chosen"][l, i] = best
+                _, p, c, q, x = orc.update(ts.mode, q, pp, cp, cs.cpos[l, best, :, i],
+                                           cs.ccov[l, best, :, i])
+                chi2 += x
+        out["par"][:, i], out["cov"][:, i], out["chi2"][i] = p, c, chi2
+    return out
+
+
+def pin_find_layerwise(orc):
+    """orc_find equals the composition of the pinned single steps with the
+    argmin over candidates, on noisy candidates that make it choose noise,
+    nothing and the track's own hit."""
+    for mode in (MODE_R, MODE_Z):
+        ts = gen.generate(mode, 12, seed=21, nlayer=4)
+        cs = gen.generate_candidates(ts, 3, seed=21, spread=3.0, p_true=0.7)
+        got = orc.find(mode, ts.B, ts.surf, ts.par0, ts.cov0, ts.q, cs.cpos, cs.ccov, 30.0)
+        ref = _find_layerwise(orc, ts, cs, 30.0)
+        assert np.array_equal(got["chosen"], ref["chosen"])
+        assert (got["chosen"] >= 0).any() and (got["chosen"] != cs.true_slot).any()
+        for k in ("par", "cov", "chi2"):
+            assert np.allclose(got[k], ref[k], rtol=1e-13, atol=1e-15), k
+
+
+def pin_find_single_candidate(orc):
+    """One candidate, the track's own hit, and no gate: the plain fit, bit for
+    bit."""
+    for mode in (MODE_R, MODE_Z):
+        ts = gen.generate(mode, 100, seed=22)
+        got = orc.find(mode, ts.B, ts.surf, ts.par0, ts.cov0, ts.q, ts.hpos[:, None],
+                       ts.hcov[:, None], 1e300)
+        ref = orc.fit_set(ts, want_layers=True)
+        for k in ("par", "cov", "q", "chi2", "chi2_layer", "status"):
+            assert np.array_equal(got[k], ref[k]), k
+        assert (got["chosen"] == 0).all()
+
+
+def pin_find_nothing_under_gate(orc):
+    """No candidate under the gate: no update, the state is the propagation."""
+    ts = gen.generate(MODE_R, 10, seed=23, nlayer=5)
+    cs = gen.generate_candidates(ts, 2, seed=23, spread=1e4, p_true=0.0)
+    got = orc.find(MODE_R, ts.B, ts.surf, ts.par0, ts.cov0, ts.q, cs.cpos, cs.ccov, 30.0)
+    assert (got["chosen"] == -1).all() and (got["chi2"] == 0).all()
+    assert (got["cand_chi2"] >= 30.0).all()
+    for i in range(ts.n):
+        p, c = ts.par0[:, i].astype(np.float64), ts.cov0[:, i].astype(np.float64)
+        for l in range(5):
+            _, p, c = orc.propagate(MODE_R, ts.B, float(ts.surf[l]), int(ts.q[i]), p, c)
+        assert np.allclose(got["par"][:, i], p, rtol=1e-14) and np.allclose(got["cov"][:, i], c, rtol=1e-14)
+
+
+def pin_find_separated_candidates(orc):
+    """Noise far from the track's hit: the track's hit is found on > 99.9 % of
+    layers."""
+    ts = gen.generate(MODE_Z, 500, seed=24)
+    cs = gen.generate_candidates(ts, 4, seed=24, spread=1e3, p_true=1.0)
+    got = orc.find(MODE_Z, ts.B, ts.surf, ts.par0, ts.cov0, ts.q, cs.cpos, cs.ccov, 30.0)
+    assert np.mean(got["chosen"] == cs.true_slot) > 0.999
+
+
 ALL_PINS = [
     pin_helix_equation_of_motion,
     pin_helix_geometry,
@@ -466,4 +550,8 @@ ALL_PINS = [
     pin_no_intersection,
     pin_filter_consistency,
     pin_chi2_gradient_fd,
+    pin_find_layerwise,
+    pin_find_single_candidate,
+    pin_find_nothing_under_gate,
+    pin_find_separated_candidates,
 ]

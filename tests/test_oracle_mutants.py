@@ -31,6 +31,13 @@ MUTANTS = {
                           "K[i][a] = CHt[i][0] * Si[0][a] + CHt[i][0] * Si[1][a];"),
     "chi2_missing_offdiagonal": ("chi2 = chi2 + r[a] * Si[a][b] * r[b];",
                                  "if (a == b) chi2 = chi2 + r[a] * Si[a][b] * r[b];"),
+    "find_takes_the_largest_chi2": ("if (value(c) < best_chi2) {", "if (value(c) > best_chi2) {"),
+    "find_updates_with_the_first_candidate": (
+        "T c = kalman_update(mode, t, cpos[l * ncand + best], ccov[l * ncand + best], st);",
+        "T c = kalman_update(mode, t, cpos[l * ncand], ccov[l * ncand], st);"),
+    "find_tries_candidates_on_the_track": (
+        "T c = kalman_update(mode, trial, cpos[l * ncand + k], ccov[l * ncand + k], ignored);",
+        "T c = kalman_update(mode, t, cpos[l * ncand + k], ccov[l * ncand + k], ignored);"),
 }
 
 
