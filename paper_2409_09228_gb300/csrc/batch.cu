@@ -188,7 +188,11 @@ int build_items(fit_plan* p, int tpb) {
   }
   if (items.size() > 0x7fffffff) return fail(FIT_ERR_ARG, "fit_plan: too many work items");
   DeviceGuard g(p->h->device);
-  if (p->d_items) cudaFree(p->d_items);
+  if (p->d_items) {  // a run of the old shape may still read them
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "fit_plan: synchronize");
+    cudaFree(p->d_items);
+  }
   p->d_items = nullptr;
   p->nitems = (int)items.size();
   p->items_tpb = tpb;

@@ -553,9 +553,15 @@ uint64_t splitmix64(uint64_t& x) {
   return z ^ (z >> 31);
 }
 
+// Grows the partials buffer; earlier asynchronous calls may still read the old
+// one, so the device is drained first.
 int ensure_partials(fit_mlp* m, int64_t nblk) {
   if (nblk <= m->partial_blocks) return FIT_OK;
-  if (m->d_partials) cudaFree(m->d_partials);
+  if (m->d_partials) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "fit_mlp: synchronize");
+    cudaFree(m->d_partials);
+  }
   m->d_partials = nullptr;
   m->partial_blocks = 0;
   cudaError_t e = cudaMalloc(&m->d_partials, (size_t)nblk * kPartial * sizeof(float));
@@ -754,6 +760,7 @@ int fit_mlp_train(fit_mlp* m, const float* x, const float* target, int64_t n,
   int rc = ensure_partials(m, nblk);
   if (rc != FIT_OK) return rc;
   if (cfg->epochs > m->curve_cap) {
+    if (m->d_curve) cudaDeviceSynchronize();
     cudaFree(m->d_curve);
     m->d_curve = nullptr;
     m->curve_cap = 0;
