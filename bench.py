@@ -39,11 +39,12 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 
 # Algorithmic work per track-layer: FP32 flops of the kernel's formulas (FMA
 # = 2), as executed with one track per thread and counted by ncu (FFMA x 2 +
-# FADD + FMUL thread instructions, 20-event workload, 2.007 p2r iterations per
-# track-layer; profiles/fit_fused_*_100x9600x20.md), and bytes (hit 36 B +
-# track state in and out 229 B / nlayer).
+# FADD + FMUL thread instructions, 20-event workload; p2r from the closed-form
+# crossing start, one path-length iteration per track-layer;
+# profiles/fit_fused_*_100x9600x20.md), and bytes (hit 36 B + track state in
+# and out 229 B / nlayer).
 FLOPS_P2Z = 489.0
-FLOPS_P2R = 723.0
+FLOPS_P2R = 700.0
 BYTES_TRACK_IN = (6 + 21 + 1) * 4
 BYTES_TRACK_OUT = (6 + 21 + 1 + 1) * 4 + 1
 
@@ -592,11 +593,12 @@ def bench_find(args, world, rank, local):
 def bench_seed(args, world, rank, local):
     """The learned p2r path-length seed.  Trains the network on 4M single p2r
     propagations labelled by the library's own exact iteration (run to
-    1e-7 R), then fits 1M p2r tracks x 20 layers with the straight-line seed
-    (the packed two-tracks-per-thread kernel) and with the network (one track
-    per thread, the network before every layer), and times the path-length
-    step alone on 4M states with each seed.  The value is the seeded fit's
-    throughput; the line carries the plain fit's beside it."""
+    1e-7 R), then fits 1M p2r tracks x 20 layers with the straight-line start
+    (the packed two-tracks-per-thread kernel), with the network (one track
+    per thread, the network before every layer) and with the closed-form
+    crossing start (packed kernel), and times the path-length step alone on
+    4M states with each start.  The value is the seeded fit's throughput; the
+    line carries the other two beside it."""
     import torch
     from paper_2409_09228_gb300 import fit, inputs
 
@@ -626,7 +628,11 @@ def bench_seed(args, world, rank, local):
                               lr_final=1e-6, seed=4, stream=stream)
     train_s = time.perf_counter() - t0
     del x, t
-    f = fit.Fitter(fit.Geometry(inputs.B_FIELD, surf), None, device=local)
+    # the network replaces the straight-line start; fc starts at the closed-form crossing
+    f = fit.Fitter(fit.Geometry(inputs.B_FIELD, surf, start=fit.FIT_START_LINE), None,
+                   device=local)
+    fc = fit.Fitter(fit.Geometry(inputs.B_FIELD, surf, start=fit.FIT_START_CROSSING), None,
+                    device=local)
     fit.fit_mlp_attach(f.h, m, stream=stream)
     # the path-length step alone, held-out states
     ss, par, q, R, h_ex, xe, _ = labelled(4_000_000, 400 + 1000 * rank)
@@ -635,8 +641,8 @@ def bench_seed(args, world, rank, local):
     hl = torch.empty(ss.n, device=dev)
     its = torch.empty(ss.n, dtype=torch.int32, device=dev)
 
-    def step_alone(seeded):
-        fit.fit_path_lengths(f.h, par, q, R, hl, its, seeded=seeded, stream=stream)
+    def step_alone(fitter, seeded):
+        fit.fit_path_lengths(fitter.h, par, q, R, hl, its, seeded=seeded, stream=stream)
 
     def timed(fn, reps):
         for _ in range(args.warmup):
@@ -651,9 +657,10 @@ def bench_seed(args, world, rank, local):
         return e0.elapsed_time(e1) / reps
 
     alone = {}
-    for seeded in (False, True):
-        ms = timed(lambda: step_alone(seeded), args.steps)
-        alone["network" if seeded else "straight_line"] = {
+    for label, fitter, seeded in (("straight_line", f, False), ("network", f, True),
+                                  ("crossing", fc, False)):
+        ms = timed(lambda: step_alone(fitter, seeded), args.steps)
+        alone[label] = {
             "ms": ms, "iterations_per_state": float(its.double().mean().item()),
             "one_iteration": float((its == 1).double().mean().item()),
             "max_abs_dh_vs_1e-7_iteration_cm": float((hl - h_ex).abs().max().item())}
@@ -682,11 +689,12 @@ def bench_seed(args, world, rank, local):
     out = f.outputs(n, ld=ld)
     res = {}
     clk = None
-    for label, net in (("straight_line", None), ("network", m)):
-        fit.fit_mlp_attach(f.h, net, stream=stream)
+    for label, fitter, net in (("straight_line", f, None), ("network", f, m),
+                               ("crossing", fc, None)):
+        fit.fit_mlp_attach(fitter.h, net, stream=stream)
         for _ in range(args.warmup):
-            f.run(*d, [n], [0], out=out, stream=stream)
-        f.sync(stream)
+            fitter.run(*d, [n], [0], out=out, stream=stream)
+        fitter.sync(stream)
         barrier(world)
         if net is not None:
             clocks = ClockSampler(local)
@@ -695,17 +703,18 @@ def bench_seed(args, world, rank, local):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            f.run(*d, [n], [0], out=out, stream=stream)
+            fitter.run(*d, [n], [0], out=out, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         if net is not None:
             clk = clocks.stop()
-        st = f.sync(stream)
+        st = fitter.sync(stream)
         assert st["nonfinite"] == 0 and st["no_intersection"] == 0 and st["not_converged"] == 0, st
         ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
         res[label] = {"ms": ms, "value": world * n * NLAYER / (ms / 1e3),
                       "iterations_per_track_layer": st["iterations"] / (args.steps * n * NLAYER)}
     f.close()
+    fc.close()
     fit.fit_mlp_destroy(m)
     if rank != 0:
         return
@@ -728,6 +737,7 @@ def bench_seed(args, world, rank, local):
                          "network_tensor_tflops": mlp_flops * tl / (ms / 1e3) / 1e12},
             "clocks": clk, "gpu_launches": args.steps,
             "plain_fit": res["straight_line"], "seeded_fit": res["network"],
+            "crossing_start_fit": res["crossing"],
             "path_length_step_alone_4M_states": alone, "held_out_seed_error": seed_err,
             "training": {"samples": args.seed_train_samples, "epochs": args.seed_epochs,
                          "batch": 4096, "seconds": train_s, "final_loss": float(curve[-1])}}
@@ -843,7 +853,7 @@ def main():
     units_per_step = 2 * n * NLAYER
     value = world * units_per_step / (ms / 1e3)
 
-    # iterations of the p2r path-length step (the flop count assumes 2.007)
+    # iterations of the p2r path-length step (the flop count assumes 1.0)
     it_per = st.get("iterations", 0) / max(1, args.steps * n * NLAYER) if "iterations" in st else None
     flops = [FLOPS_P2R, FLOPS_P2Z]
     dom = int(np.argmax(kernel_ms))

@@ -69,7 +69,21 @@ typedef struct {
                         [cm], in the order the tracks cross them; copied */
   int max_iter;      /* p2r: maximum path-length iterations (<= 0: 10) */
   float tol;         /* p2r: stop when a step is <= tol * R (<= 0: 1e-6) */
+  int start;         /* p2r: where the path-length iteration starts, a FIT_START_*
+                        value; 0 (a zeroed struct) is FIT_START_CROSSING */
 } fit_config;
+
+/* Start of the p2r path-length iteration (Sec. 3.2: the iteration advances
+ * the track in straight-line steps to the cylinder).  Both converge to the
+ * same crossing under the same tolerance; they differ in the steps taken.
+ *   FIT_START_CROSSING: the crossing of the track's transverse circle with the
+ *     cylinder in closed form (a quadratic in tan of half the turning angle),
+ *     where the start is inside the cylinder and the track turns by less than
+ *     0.49 rad on the way; the first step then confirms it.  Elsewhere, the
+ *     straight-line start.
+ *   FIT_START_LINE: the straight-line distance along the initial direction. */
+#define FIT_START_CROSSING 0
+#define FIT_START_LINE 1
 
 typedef struct fit_handle fit_handle;
 
@@ -503,7 +517,7 @@ int fit_mlp_attach(fit_handle* h, const fit_mlp* m, void* stream);
  * handle's p2r tolerance and iteration limit: h_out [n] the path length
  * (NaN when the cylinder is not reached), iters_out [n] (may be NULL) the
  * iterations taken.  seeded = 1 starts from the attached network (FIT_ERR_ARG
- * if none), 0 from the straight line.  All DEVICE.
+ * if none), 0 from the handle's p2r start (fit_config.start).  All DEVICE.
  */
 int fit_path_lengths(fit_handle* h, const float* par, int64_t ld, const int32_t* q,
                      const float* R, int64_t n, float* h_out, int32_t* iters_out, int seeded,

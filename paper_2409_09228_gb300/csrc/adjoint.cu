@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(kAdjBlock) fit_tape_kernel(const __grid_consta
     if (MODE == FIT_MODE_Z)
       fail = fitk::prop_z(s.p, s.c, s.g, dkdw, sf);
     else
-      fail = fitk::prop_r(s.p, s.c, s.g, dkdw, sf, a.geo.max_iter, a.geo.tol * sf, iters, nc);
+      fail = fitk::prop_r(s.p, s.c, s.g, dkdw, sf, a.geo.max_iter, a.geo.tol * sf,
+                          a.geo.line_start, iters, nc);
     if (fail) {
       st |= FIT_ST_NO_INTERSECTION;
       break;
@@ -142,7 +143,8 @@ __global__ void __launch_bounds__(kAdjBlock) fit_adjoint_kernel(const __grid_con
     if (MODE == FIT_MODE_Z)
       fitk::prop_z(p1, c1, g, dkdw, sf);
     else
-      fitk::prop_r(p1, c1, g, dkdw, sf, b.geo.max_iter, b.geo.tol * sf, iters, nc);
+      fitk::prop_r(p1, c1, g, dkdw, sf, b.geo.max_iter, b.geo.tol * sf, b.geo.line_start, iters,
+                   nc);
     float pb1[6], cb1[21], mb[3];
     if (MODE == FIT_MODE_Z)
       fitk::update_z_bwd(p1, c1, m, v, pb, cb, wgt, pb1, cb1, mb);
@@ -153,7 +155,8 @@ __global__ void __launch_bounds__(kAdjBlock) fit_adjoint_kernel(const __grid_con
     if (MODE == FIT_MODE_Z)
       fitk::prop_z_bwd(p, c, dkdw, sf, pb1, cb1, pb, cb);
     else
-      fitk::prop_r_bwd(p, c, dkdw, sf, b.geo.max_iter, b.geo.tol * sf, pb1, cb1, pb, cb);
+      fitk::prop_r_bwd(p, c, dkdw, sf, b.geo.max_iter, b.geo.tol * sf, b.geo.line_start, pb1, cb1,
+                       pb, cb);
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) b.g_par0[k * ld + t] = pb[k];

@@ -201,7 +201,7 @@ __device__ __forceinline__ void prop_z_bwd(const float (&p)[6], const float (&c)
 // ---- propagation to a cylinder ------------------------------------------
 // Returns false if the cylinder is not reached (nothing is written then).
 __device__ __forceinline__ bool prop_r_bwd(const float (&p)[6], const float (&c)[21], float dkdw,
-                                           float R, int max_iter, float tol_abs,
+                                           float R, int max_iter, float tol_abs, bool line_start,
                                            const float (&pbo)[6], const float (&cbo)[21],
                                            float (&pb)[6], float (&cb)[21]) {
   Trig<float> g = trig_of(p);
@@ -209,7 +209,7 @@ __device__ __forceinline__ bool prop_r_bwd(const float (&p)[6], const float (&c)
   unsigned iters[1] = {0u};
   bool notconv = false;
   PathR<float> w;
-  if (path_r(p, g, kappa, R, max_iter, tol_abs, iters, notconv, w)) return false;
+  if (path_r(p, g, kappa, R, max_iter, tol_abs, line_start, iters, notconv, w)) return false;
   // Everything below is an explicit function of (p, h) at the final h.
   const float h = w.h;
   const float sph = g.sphi, cph = g.cphi, sth = g.sth, cth = g.cth;

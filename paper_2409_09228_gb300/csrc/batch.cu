@@ -39,8 +39,12 @@ struct BatchArgs {
   unsigned* work_counter;
 };
 
+// At least 384 resident threads per SM (3 blocks of 128, 6 of 64), as for
+// fit_fused_kernel's p2r: left free, the compiler takes ~190 registers and
+// only 2 blocks of 128 fit.
 template <int BLK>
-__global__ void __launch_bounds__(BLK) fit_batched_kernel(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(BLK, 384 / BLK)
+    fit_batched_kernel(const __grid_constant__ BatchArgs b) {
   __shared__ int s_item;
   for (;;) {
     __syncthreads();  // every thread has read the previous item index
@@ -67,7 +71,8 @@ __global__ void __launch_bounds__(BLK) fit_batched_kernel(const __grid_constant_
 // Same-mode runs of events, one launch each (the fit_propagate_update path),
 // kept as an autotuner candidate: for few, large events it can win.
 template <int MODE>
-__global__ void __launch_bounds__(kBlock) fit_segment_kernel(const __grid_constant__ FitArgs a) {
+__global__ void __launch_bounds__(kBlock, MODE == FIT_MODE_Z ? 4 : 3)
+    fit_segment_kernel(const __grid_constant__ FitArgs a) {
   const int64_t t = pair_track(a);
   if (t >= a.t1) return;
   unsigned st[2] = {0u, 0u}, iters[2] = {0u, 0u};

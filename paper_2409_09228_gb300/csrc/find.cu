@@ -61,57 +61,85 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
   unsigned st = 0u, iters[1] = {0u};
   const Geo& geo = a.geo;
   const int64_t ldc = a.ld_cand;
+  // The layer loop runs the p2r crossing start in its series form only
+  // (Start::kFast).  A surface where that form does not apply ends the inner
+  // loop; the outer one then propagates to it from crossing_exact's start and
+  // resumes the inner loop at its candidates.  Kept out of the inner loop,
+  // the exact form costs the loop nothing (inside it, 20 %).
   int l = 0;
-  for (; l < a.nlayer; ++l) {
+  bool propagated = false;  // layer l's propagation is done
+  for (;;) {
+    bool rerun = false;
+    for (; l < a.nlayer; ++l) {
+      const float sf = geo.surf.s[l];
+      const T dkdw = qf * -a.kB;
+      bool nc = false, failed = false;
+      if (propagated)
+        propagated = false;
+      else if (MODE == FIT_MODE_Z)
+        failed = fitk::prop_z(p, c, g, dkdw, sf);
+      else
+        failed = fitk::prop_r<T, false, fitk::Start::kFast>(p, c, g, dkdw, sf, geo.max_iter,
+                                                             geo.tol * sf, geo.line_start, iters,
+                                                             nc);
+      if (failed) {
+        if (MODE == FIT_MODE_R && !geo.line_start)
+          rerun = true;
+        else
+          st |= FIT_ST_NO_INTERSECTION;
+        break;
+      }
+      if (nc) st |= FIT_ST_NOT_CONVERGED;
+      const T* cp = a.cpos + (int64_t)l * a.ncand * 3 * ldc + t;
+      const T* cc = a.ccov + (int64_t)l * a.ncand * 6 * ldc + t;
+      int best = -1;
+      T best_chi2 = a.gate;
+      for (int k = 0; k < a.ncand; ++k) {
+        T m[3], v[6];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) fitk::ld(m[j], cp + (3 * k + j) * ldc);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) fitk::ld(v[j], cc + (6 * k + j) * ldc);
+        const T x = (MODE == FIT_MODE_Z) ? fitk::chi2_z(p, c, m, v) : fitk::chi2_r(p, c, m, v);
+        if (x < best_chi2) {
+          best = k;
+          best_chi2 = x;
+        }
+      }
+      a.chosen[(int64_t)l * a.ld_out + t] = (int8_t)best;
+      T x2 = T(0.f);
+      if (best >= 0) {
+        T m[3], v[6];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) fitk::ld(m[j], cp + (3 * best + j) * ldc);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) fitk::ld(v[j], cc + (6 * best + j) * ldc);
+        const T phi_pred = p[4], th_pred = p[5];
+        x2 = (MODE == FIT_MODE_Z) ? fitk::update_z(p, c, m, v) : fitk::update_r(p, c, m, v);
+        if (fitk::normalise(p, c, qf, g, phi_pred, th_pred)) st |= FIT_ST_CHARGE_FLIP;
+        if (!fitk::finite_(x2)) {
+          st |= FIT_ST_NONFINITE;
+          x2 = T(0.f);
+          if (a.chi2_layer) a.chi2_layer[(int64_t)l * a.ld_out + t] = x2;
+          ++l;
+          break;
+        }
+      }
+      chi2 += x2;
+      if (a.chi2_layer) a.chi2_layer[(int64_t)l * a.ld_out + t] = x2;
+    }
+    if (!rerun) break;
     const float sf = geo.surf.s[l];
     const T dkdw = qf * -a.kB;
-    bool nc = false, failed;
-    if (MODE == FIT_MODE_Z)
-      failed = fitk::prop_z(p, c, g, dkdw, sf);
-    else
-      failed = fitk::prop_r(p, c, g, dkdw, sf, geo.max_iter, geo.tol * sf, iters, nc);
-    if (failed) {
+    const T h0 = fitk::crossing_exact<T>(p[0], p[1], g.cphi, g.sphi, dkdw * p[3], T(sf));
+    bool nc = false;
+    if (fitk::prop_r<T, false, fitk::Start::kGiven>(p, c, g, dkdw, sf, geo.max_iter,
+                                                    geo.tol * sf, false, iters, nc, T(0.f), h0)) {
       st |= FIT_ST_NO_INTERSECTION;
       break;
     }
     if (nc) st |= FIT_ST_NOT_CONVERGED;
-    const T* cp = a.cpos + (int64_t)l * a.ncand * 3 * ldc + t;
-    const T* cc = a.ccov + (int64_t)l * a.ncand * 6 * ldc + t;
-    int best = -1;
-    T best_chi2 = a.gate;
-    for (int k = 0; k < a.ncand; ++k) {
-      T m[3], v[6];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) fitk::ld(m[j], cp + (3 * k + j) * ldc);
-#pragma unroll
-      for (int j = 0; j < 6; ++j) fitk::ld(v[j], cc + (6 * k + j) * ldc);
-      const T x = (MODE == FIT_MODE_Z) ? fitk::chi2_z(p, c, m, v) : fitk::chi2_r(p, c, m, v);
-      if (x < best_chi2) {
-        best = k;
-        best_chi2 = x;
-      }
-    }
-    a.chosen[(int64_t)l * a.ld_out + t] = (int8_t)best;
-    T x2 = T(0.f);
-    if (best >= 0) {
-      T m[3], v[6];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) fitk::ld(m[j], cp + (3 * best + j) * ldc);
-#pragma unroll
-      for (int j = 0; j < 6; ++j) fitk::ld(v[j], cc + (6 * best + j) * ldc);
-      const T phi_pred = p[4], th_pred = p[5];
-      x2 = (MODE == FIT_MODE_Z) ? fitk::update_z(p, c, m, v) : fitk::update_r(p, c, m, v);
-      if (fitk::normalise(p, c, qf, g, phi_pred, th_pred)) st |= FIT_ST_CHARGE_FLIP;
-      if (!fitk::finite_(x2)) {
-        st |= FIT_ST_NONFINITE;
-        x2 = T(0.f);
-        if (a.chi2_layer) a.chi2_layer[(int64_t)l * a.ld_out + t] = x2;
-        ++l;
-        break;
-      }
-    }
-    chi2 += x2;
-    if (a.chi2_layer) a.chi2_layer[(int64_t)l * a.ld_out + t] = x2;
+    propagated = true;
   }
   for (int r = l; r < a.nlayer; ++r) {  // layers not reached
     a.chosen[(int64_t)r * a.ld_out + t] = -1;

@@ -29,7 +29,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 namespace {
 
-// 3 resident blocks per SM for p2r (167 registers, no spills); p2z fits 4
+// 3 resident blocks per SM for p2r (168 registers, no spills); p2z fits 4
 // (128 registers, 16 bytes of spill), which was 3 % faster than 3.
 template <int MODE, int L = 0>
 __global__ void __launch_bounds__(kBlock, MODE == FIT_MODE_Z ? 4 : 3)
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kBlock, MODE == FIT_MODE_Z ? 4 : 3)
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, MODE == FIT_MODE_Z ? 4 : 3)
     fit_fused_kernel_noalloc(const __grid_constant__ FitArgs a, const int64_t* __restrict__ evt_off,
                              int e0, int e1) {
   const int64_t t = pair_track(a);
@@ -83,6 +83,9 @@ int configure_modes(fit_handle* h, const fit_config* cfg_r, const fit_config* cf
     h->B[m] = c->B;
     h->geo[m].max_iter = c->max_iter > 0 ? c->max_iter : 10;
     h->geo[m].tol = c->tol > 0.f ? c->tol : 1e-6f;
+    if (c->start != FIT_START_CROSSING && c->start != FIT_START_LINE)
+      return fail(FIT_ERR_ARG, std::string(who) + ": start is not a FIT_START_* value");
+    h->geo[m].line_start = c->start == FIT_START_LINE;
   }
   return FIT_OK;
 }

@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(kBlock) fit_f64_kernel(const __grid_constant__
     if (MODE == FIT_MODE_Z)
       failed = fitk::prop_z(p, c, g, dkdw, sf);
     else
-      failed = fitk::prop_r(p, c, g, dkdw, sf, geo.max_iter, geo.tol * sf, iters, nc);
+      failed = fitk::prop_r(p, c, g, dkdw, sf, geo.max_iter, geo.tol * sf,
+                            geo.line_start, iters, nc);
     if (failed) {
       st |= FIT_ST_NO_INTERSECTION;
       if (a.chi2_layer)

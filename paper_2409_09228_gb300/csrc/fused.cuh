@@ -135,7 +135,8 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
     if (MODE == FIT_MODE_Z)
       fail = fitk::prop_z(s.p, s.c, s.g, dkdw, sf);
     else
-      fail = fitk::prop_r(s.p, s.c, s.g, dkdw, sf, geo.max_iter, geo.tol * sf, iters, nc);
+      fail = fitk::prop_r(s.p, s.c, s.g, dkdw, sf, geo.max_iter, geo.tol * sf,
+                          geo.line_start, iters, nc);
     if (fitk::any(fitk::and_(fail, alive))) return l;
     const T phi_pred = s.p[4], th_pred = s.p[5];
     T x2 = (MODE == FIT_MODE_Z) ? fitk::update_z(s.p, s.c, m, v) : fitk::update_r(s.p, s.c, m, v);
@@ -181,8 +182,9 @@ __device__ __forceinline__ void finish_one(const FitArgs& a, const Geo& geo, int
 }
 
 // Tracks t and t+1 of the range [t0, t1) (t even).  Both valid: the pair
-// shares packed instructions until a surface that one of them cannot reach,
-// from where each finishes alone.  One valid (the range starts or ends at an
+// shares packed instructions until a surface that one of them cannot reach
+// (or, for p2r, whose crossing needs the one-lane form of the closed-form
+// start), from where each finishes alone.  One valid (the range starts or ends at an
 // odd index): that one alone.
 template <int MODE, int L = 0>
 __device__ __forceinline__ void run_pair(const FitArgs& a, const Geo& geo, int64_t t0, int64_t t1,

@@ -29,6 +29,7 @@ struct Geo {
   float kB;  // kA * B
   int max_iter;
   float tol;
+  int line_start;  // p2r: start the path-length iteration at the straight-line step
   Surfaces surf;
 };
 

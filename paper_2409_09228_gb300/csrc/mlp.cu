@@ -430,9 +430,9 @@ __global__ void __launch_bounds__(kAdamThreads)
 template <bool SEED>
 __global__ void __launch_bounds__(kBlock)
     path_length_kernel(const Image* __restrict__ img, float kB, int max_iter, float tol,
-                       const float* __restrict__ par, int64_t ld, const int32_t* __restrict__ q,
-                       const float* __restrict__ R, int64_t n, float* __restrict__ h_out,
-                       int32_t* __restrict__ it_out) {
+                       bool line_start, const float* __restrict__ par, int64_t ld,
+                       const int32_t* __restrict__ q, const float* __restrict__ R, int64_t n,
+                       float* __restrict__ h_out, int32_t* __restrict__ it_out) {
   __shared__ Image W;
   __shared__ uint4 stage[kBlock / 32][64];
   if (SEED) {
@@ -461,7 +461,8 @@ __global__ void __launch_bounds__(kBlock)
   bool nc = false;
   fitk::PathR<float> w;
   const bool failed =
-      fitk::path_r<float, SEED>(p, g, -qf * kB * p[3], Ri, max_iter, tol * Ri, it, nc, w, gs);
+      fitk::path_r<float, SEED>(p, g, -qf * kB * p[3], Ri, max_iter, tol * Ri, line_start, it,
+                                nc, w, gs);
   h_out[i] = failed ? __int_as_float(0x7fc00000) : w.h;
   if (it_out) it_out[i] = failed ? 0 : (int32_t)it[0];
 }
@@ -512,7 +513,7 @@ __global__ void __launch_bounds__(kBlock) fit_seeded_kernel(const __grid_constan
     for (int k = 0; k < 6; ++k) fitk::ld(v[k], a.hcov + (6 * l + k) * ldh + t);
     bool nc = false;
     const bool failed = fitk::prop_r<float, true>(s.p, s.c, s.g, s.qf * -geo.kB, sf, geo.max_iter,
-                                                  geo.tol * sf, iters, nc, gs);
+                                                  geo.tol * sf, false, iters, nc, gs);
     if (failed) {
       st |= FIT_ST_NO_INTERSECTION;
       if (a.chi2_layer)
@@ -839,10 +840,12 @@ int fit_path_lengths(fit_handle* h, const float* par, int64_t ld, const int32_t*
   const Image* img = static_cast<const Image*>(h->d_mlp);
   if (seeded)
     path_length_kernel<true><<<(unsigned)nblk, kBlock, 0, s>>>(
-        img, geo.kB, geo.max_iter, geo.tol, par, ld, q, R, n, h_out, iters_out);
+        img, geo.kB, geo.max_iter, geo.tol, geo.line_start != 0, par, ld, q, R, n, h_out,
+        iters_out);
   else
     path_length_kernel<false><<<(unsigned)nblk, kBlock, 0, s>>>(
-        img, geo.kB, geo.max_iter, geo.tol, par, ld, q, R, n, h_out, iters_out);
+        img, geo.kB, geo.max_iter, geo.tol, geo.line_start != 0, par, ld, q, R, n, h_out,
+        iters_out);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FIT_OK : cuda_fail(e, "fit_path_lengths: launch");
 }

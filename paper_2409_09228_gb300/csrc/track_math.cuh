@@ -308,14 +308,120 @@ __device__ __forceinline__ typename Lanes<T>::M prop_z(T (&p)[6], T (&c)[21], Tr
   return fail;
 }
 
+// atan(t) / t: its Taylor series to t^12 (remainder below 2.5e-10 for
+// |t| <= 1/4, the range crossing_start admits); in double atan itself.
+template <class T>
+__device__ __forceinline__ T atan_ratio(T t) {
+  const T t2 = t * t;
+  return fma(t2, fma(t2, fma(t2, fma(t2, fma(t2, fma(t2, T(1.f / 13.f), T(-1.f / 11.f)),
+                                             T(1.f / 9.f)), T(-1.f / 7.f)), T(1.f / 5.f)),
+                      T(-1.f / 3.f)), T(1.f));
+}
+__device__ __forceinline__ double atan_ratio(double t) { return t != 0.0 ? ::atan(t) / t : 1.0; }
+
+// Where the helix of the propagation crosses the cylinder r = R, in closed
+// form.  With b0 and t0 the start's components along and across the
+// direction phi, c0 = r0^2 - R^2 and t = tan(kappa h / 2), the transverse
+// displacement over h is the chord 2 sin(kappa h / 2) / kappa at angle
+// phi + kappa h / 2, and r(h)^2 = R^2 multiplied by (1 + t^2) kappa^2 / 2 is
+// the quadratic
+//   2 F t^2 + 2 kappa b0 t + kappa^2 c0 / 2 = 0,  F = 1 + kappa (t0 + kappa c0 / 4).
+// Its discriminant is kappa^2 X with X = b0^2 - c0 F: the circle misses the
+// cylinder exactly when X < 0.  The roots are t = kappa hl / 2 with
+// hl = -c0 / (b0 +- sqrt(X)); each gives h = 2 atan(t) / kappa modulo one
+// turn, 2 pi / |kappa|, and the first forward crossing is the smaller h in
+// (0, 2 pi / |kappa|].
+//
+// crossing_exact: that first forward crossing for one lane, from any start
+// (atan2 for the angles); -1 when the cylinder is not reached.  A track
+// with |kappa| R below 1e-9 is a straight line: the smaller positive root of
+// h^2 + 2 b0 h + c0 = 0.
+template <class S>
+__device__ __noinline__ S crossing_exact(S x, S y, S cph, S sph, S kappa, S R) {
+  const S b0 = fma(x, cph, y * sph);
+  const S t0 = fma(y, cph, -(x * sph));
+  const S c0 = fma(x, x, fma(y, y, -(R * R)));
+  S best = S(-1);
+  if (fabs(kappa) * R < S(1e-9)) {
+    const S disc = fma(b0, b0, -c0);
+    if (!(disc >= S(0))) return S(-1);
+    const S qv = -(b0 + copysign(sqrt(disc), b0));
+    const S r[2] = {qv, qv != S(0) ? c0 / qv : S(0)};
+    for (int k = 0; k < 2; ++k)
+      if (r[k] > S(0) && (best < S(0) || r[k] < best)) best = r[k];
+  } else {
+    const S F = fma(kappa, fma(S(0.25) * kappa, c0, t0), S(1));
+    const S X = fma(b0, b0, -(c0 * F));
+    if (!(X >= S(0))) return S(-1);
+    const S sq = sqrt(X), num = S(-0.5) * kappa * c0;
+    const S period = S(2) * pi_<S>() / fabs(kappa);
+    for (int k = 0; k < 2; ++k) {
+      S hk = S(2) * atan2(num, k ? b0 - sq : b0 + sq) / kappa;
+      hk -= floor(hk / period) * period;
+      if (!(hk > S(0))) hk += period;
+      if (best < S(0) || hk < best) best = hk;
+    }
+  }
+  return best > S(0) ? best : S(-1);
+}
+
+// crossing_start: the same for all lanes.  From inside the cylinder
+// (c0 <= 0) with X >= 0, the root with b0 + sqrt(X) > 0 is the first forward
+// crossing: for F >= 0 the two roots in t have opposite signs and it is the
+// forward one; for F < 0 both lie on the same side, ahead of the track when
+// b0 > 0 with this one the nearer, behind it when b0 < 0, where
+// b0 + sqrt(X) < 0.  Within |t| <= 1/4 (a turn below 0.49 rad) atan(t) / t
+// is its series and h = hl atan(t) / t costs one square root and one
+// division.  Returns the lanes that cannot reach the cylinder.  Every other
+// lane needs crossing_exact: with EXACT a one-lane type calls it here;
+// otherwise, and always for packed lanes (F2), such a lane is returned as
+// failing and its caller reruns the surface for it (the fused kernel
+// propagates each track of the pair alone from there; a call inside the
+// packed loop cost it registers on every layer).
+template <class T, bool EXACT>
+__device__ __forceinline__ typename Lanes<T>::M crossing_start(T x, T y, T cph, T sph, T kappa,
+                                                               float R, T b0, T c0, T& h) {
+  using M = typename Lanes<T>::M;
+  const T t0 = fma(y, cph, -(x * sph));
+  const T F = fma(kappa, fma(T(0.25f) * kappa, c0, t0), T(1.f));
+  const T X = fma(b0, b0, -(c0 * F));
+  const T den = b0 + fsqrt(X);
+  const T hl = fdiv(-c0, den);
+  const T t = T(0.5f) * kappa * hl;
+  const M ok = and_(and_(le(c0, T(0.f)), le(T(0.f), X)),
+                    and_(lt(T(0.f), den), le(fabs_(t), T(0.25f))));
+  h = hl * atan_ratio(t);
+  if constexpr (Lanes<T>::n > 1 || !EXACT) {
+    return not_(ok);
+  } else {
+    if (ok) return false;
+    h = crossing_exact<T>(x, y, cph, sph, kappa, T(R));
+    return !(h > T(0));
+  }
+}
+
 // Path length to the cylinder r = R by straight-line steps along the current
-// direction: the first step from (x, y) along phi, then repeatedly the helix
-// at h and a straight step along its direction to the circle, until a step is
-// below tol_abs.  Returns the mask of lanes that cannot reach the cylinder
-// (the other outputs are then meaningless).  On return h is the path length;
+// direction: from a start h, repeatedly the helix at h and a straight step
+// along its direction to the circle, until a step is below tol_abs.  With
+// line_start (and with SEEDED) the start is the straight-line distance from
+// (x, y) along phi, and a lane whose straight line misses the circle, or that
+// starts outside moving outwards, counts as not reaching it.  Otherwise the
+// start is the closed-form crossing (crossing_start), which decides
+// reachability exactly, and one evaluation confirms it.  Returns the mask of
+// lanes that cannot reach the cylinder (the other outputs are then
+// meaningless); with packed lanes also those that need the one-lane form of
+// the crossing start.  On return h is the path length;
 // the helix quantities (u, s, cu, cm, sm, px, py, c1, s1) are those of the
 // last evaluation, at h - d.  iters[i] counts lane i's iterations; notconv
 // marks lanes that reached max_iter.
+// Where path_r starts when line_start is not set.  kAuto: the closed-form
+// crossing (crossing_start), in its exact form where a one-lane type needs it.
+// kFast: the series form only; a lane that needs the exact form is returned
+// as failing, so that the caller can rerun the surface with kGiven from
+// crossing_exact outside its hot loop (a call or the exact form's code inside
+// that loop slowed the memory-bound finder by 20 %).  kGiven: h_given.
+enum class Start { kAuto, kFast, kGiven };
+
 template <class T>
 struct PathR {
   T h, d, u, s, cu, cm, sm, px, py, c1, s1;
@@ -327,37 +433,49 @@ struct PathR {
 // h_line when the start is inside the cylinder and that value is finite and
 // within h_line / 4 of h_line.  The iteration, its tolerance and its result
 // are otherwise unchanged.
-template <class T, bool SEEDED = false>
+template <class T, bool SEEDED = false, Start START = Start::kAuto>
 __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Trig<T>& g, T kappa,
                                                        float R, int max_iter, float tol_abs,
+                                                       bool line_start,
                                                        unsigned (&iters)[Lanes<T>::n],
                                                        typename Lanes<T>::M& notconv, PathR<T>& w,
-                                                       T gseed = T(0.f)) {
+                                                       T gseed = T(0.f), T h_given = T(0.f)) {
   using M = typename Lanes<T>::M;
   const T sph = g.sphi, cph = g.cphi;
   const T x = p[0], y = p[1];
   const T R2 = T(R) * T(R);
-  // The transverse circle (centre c, radius rho = 1/|kappa|) reaches radius
-  // R only if |c| + rho >= R, which always holds when rho >= R.
-  M fail = lt(T(1.f), T(R) * fabs_(kappa));
-  if (any(fail)) {
-    const T irs = fdiv(T(1.f), kappa);  // signed radius
-    const T cx = fma(-sph, irs, x), cy = fma(cph, irs, y);
-    fail = and_(fail, lt(fsqrt(fma(cx, cx, cy * cy)) + fabs_(irs), T(R)));
-  }
-  // First step: along the initial direction to the circle (forward root from
-  // inside; from outside, the nearer forward root when moving inwards).
   const T b0 = fma(x, cph, y * sph);
   const T c0 = fma(x, x, fma(y, y, -R2));
-  const T disc0 = fma(b0, b0, -c0);
-  const T sq0 = fsqrt(disc0);
   const M inside = le(c0, T(0.f));
-  fail = or_(fail, or_(lt(disc0, T(0.f)), and_(not_(inside), not_(lt(b0, T(0.f))))));
-  if (any(fail)) return fail;
-  T h = sel(inside, sel(lt(T(0.f), b0), fdiv(-c0, b0 + sq0), sq0 - b0), fdiv(c0, sq0 - b0));
-  if constexpr (SEEDED) {
-    const T hs = fma(gseed * T(0.5f) * kappa, h * h, h);
-    h = sel(and_(and_(inside, finite_(hs)), le(fabs_(hs - h), T(0.25f) * h)), hs, h);
+  T h;
+  M fail;
+  if constexpr (START == Start::kGiven) {
+    h = h_given;
+    fail = not_(lt(T(0.f), h));
+    if (any(fail)) return fail;
+  } else if (SEEDED || line_start) {
+    // The transverse circle (centre c, radius rho = 1/|kappa|) reaches radius
+    // R only if |c| + rho >= R, which always holds when rho >= R.
+    fail = lt(T(1.f), T(R) * fabs_(kappa));
+    if (any(fail)) {
+      const T irs = fdiv(T(1.f), kappa);  // signed radius
+      const T cx = fma(-sph, irs, x), cy = fma(cph, irs, y);
+      fail = and_(fail, lt(fsqrt(fma(cx, cx, cy * cy)) + fabs_(irs), T(R)));
+    }
+    // First step: along the initial direction to the circle (forward root
+    // from inside; from outside, the nearer forward root when moving inwards).
+    const T disc0 = fma(b0, b0, -c0);
+    const T sq0 = fsqrt(disc0);
+    fail = or_(fail, or_(lt(disc0, T(0.f)), and_(not_(inside), not_(lt(b0, T(0.f))))));
+    if (any(fail)) return fail;
+    h = sel(inside, sel(lt(T(0.f), b0), fdiv(-c0, b0 + sq0), sq0 - b0), fdiv(c0, sq0 - b0));
+    if constexpr (SEEDED) {
+      const T hs = fma(gseed * T(0.5f) * kappa, h * h, h);
+      h = sel(and_(and_(inside, finite_(hs)), le(fabs_(hs - h), T(0.25f) * h)), hs, h);
+    }
+  } else {
+    fail = crossing_start<T, START == Start::kAuto>(x, y, cph, sph, kappa, R, b0, c0, h);
+    if (any(fail)) return fail;
   }
   // The directions phi + u and phi + 2u come from turning (cos phi, sin phi)
   // by u.  A lane that has converged keeps its h.
@@ -398,17 +516,18 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
 // Propagation to the cylinder r = R (path length from path_r).  Returns the
 // mask of lanes that cannot reach the cylinder; if any lane fails nothing is
 // modified.
-template <class T, bool SEEDED = false>
+template <class T, bool SEEDED = false, Start START = Start::kAuto>
 __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Trig<T>& g, T dkdw,
                                                        float R, int max_iter, float tol_abs,
+                                                       bool line_start,
                                                        unsigned (&iters)[Lanes<T>::n],
                                                        typename Lanes<T>::M& notconv,
-                                                       T gseed = T(0.f)) {
+                                                       T gseed = T(0.f), T h_given = T(0.f)) {
   const T x = p[0], y = p[1];
   const T kappa = dkdw * p[3];
   PathR<T> w;
-  const auto fail =
-      path_r<T, SEEDED>(p, g, kappa, R, max_iter, tol_abs, iters, notconv, w, gseed);
+  const auto fail = path_r<T, SEEDED, START>(p, g, kappa, R, max_iter, tol_abs, line_start,
+                                             iters, notconv, w, gseed, h_given);
   if (any(fail)) return fail;
   const T h = w.h, d = w.d, u = w.u, s = w.s, cu = w.cu, cm = w.cm, sm = w.sm;
   T px = w.px, py = w.py, c1 = w.c1, s1 = w.s1;

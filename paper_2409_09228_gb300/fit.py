@@ -31,6 +31,8 @@ FIT_ST_NO_INTERSECTION = 1
 FIT_ST_NOT_CONVERGED = 2
 FIT_ST_NONFINITE = 4
 FIT_ST_CHARGE_FLIP = 8
+FIT_START_CROSSING = 0
+FIT_START_LINE = 1
 FIT_MAX_LAYERS = 64
 
 
@@ -43,7 +45,7 @@ class FitError(RuntimeError):
 class fit_config(ctypes.Structure):
     _fields_ = [("B", ctypes.c_float), ("nlayer", ctypes.c_int),
                 ("surf", ctypes.POINTER(ctypes.c_float)), ("max_iter", ctypes.c_int),
-                ("tol", ctypes.c_float)]
+                ("tol", ctypes.c_float), ("start", ctypes.c_int)]
 
 
 class fit_tracks_in(ctypes.Structure):
@@ -233,13 +235,15 @@ class Geometry:
     surf: Sequence[float]
     max_iter: int = 10
     tol: float = 1e-6
+    start: int = FIT_START_CROSSING  # or FIT_START_LINE: the straight-line start
 
 
 def _config(g: Optional[Geometry]):
     if g is None:
         return None, None
     arr = (ctypes.c_float * len(g.surf))(*[float(s) for s in g.surf])
-    return fit_config(float(g.B), len(g.surf), arr, int(g.max_iter), float(g.tol)), arr
+    return fit_config(float(g.B), len(g.surf), arr, int(g.max_iter), float(g.tol),
+                      int(g.start)), arr
 
 
 def fit_init(geom_r: Optional[Geometry], geom_z: Optional[Geometry], device: int = 0) -> int:

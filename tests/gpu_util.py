@@ -23,13 +23,15 @@ def concat(sets):
 
 
 def run(sets, geom_r=None, geom_z=None, ld=None, layers=False, in_place=False, max_iter=10,
-        tol=1e-6):
+        tol=1e-6, start=fit.FIT_START_CROSSING):
     """Fits the events `sets` (one TrackSet per event) in one fit_propagate_update call."""
     B = sets[0].B
     if geom_r is None and any(s.mode == inputs.MODE_R for s in sets):
-        geom_r = fit.Geometry(B, next(s.surf for s in sets if s.mode == inputs.MODE_R), max_iter, tol)
+        geom_r = fit.Geometry(B, next(s.surf for s in sets if s.mode == inputs.MODE_R), max_iter, tol,
+                              start)
     if geom_z is None and any(s.mode == inputs.MODE_Z for s in sets):
-        geom_z = fit.Geometry(B, next(s.surf for s in sets if s.mode == inputs.MODE_Z), max_iter, tol)
+        geom_z = fit.Geometry(B, next(s.surf for s in sets if s.mode == inputs.MODE_Z), max_iter, tol,
+                              start)
     f = fit.Fitter(geom_r, geom_z)
     c = concat(sets)
     n = c["par0"].shape[-1]

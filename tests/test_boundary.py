@@ -45,6 +45,19 @@ def test_binding_names_match_header():
         assert hasattr(fit, name), f"binding lacks {name}"
 
 
+def test_binding_constants_match_header():
+    defines = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        for m in re.finditer(r"^#define (FIT_\w+) \(?(-?\d+)u?\)?", open(h).read(), re.M):
+            defines[m.group(1)] = int(m.group(2))
+    for name in ("FIT_START_CROSSING", "FIT_START_LINE", "FIT_LAYOUT_SOA", "FIT_LAYOUT_AOSOA32",
+                 "FIT_OK", "FIT_ERR_ARG", "FIT_ST_NOT_CONVERGED"):
+        assert name in defines, name
+    for name, value in defines.items():
+        if hasattr(fit, name):
+            assert getattr(fit, name) == value, name
+
+
 def test_argument_errors_without_gpu(lib):
     L = fit.load()
     h = ctypes.c_void_p()
@@ -58,8 +71,9 @@ def test_argument_errors_without_gpu(lib):
 
 def test_struct_layouts_match_header():
     # field offsets as a C compiler lays out the structs of fit.h (LP64)
-    assert ctypes.sizeof(fit.fit_config) == 24
+    assert ctypes.sizeof(fit.fit_config) == 32
     assert fit.fit_config.surf.offset == 8
+    assert fit.fit_config.start.offset == 24
     assert ctypes.sizeof(fit.fit_tracks_in) == 32
     assert ctypes.sizeof(fit.fit_tracks_out) == 56
     assert ctypes.sizeof(fit.fit_hits) == 24

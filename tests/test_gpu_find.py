@@ -167,6 +167,51 @@ def test_one_candidate_is_the_fit():
         f.close()
 
 
+def test_one_candidate_on_strongly_turning_tracks_is_the_fit():
+    """Four cylinders 70 cm apart, pT from 1.1 to 2.5 times the reach limit
+    of the outermost: between cylinders the tracks turn by up to 1 rad, and
+    on many surfaces the p2r crossing start needs its exact form, which the
+    FP32 finder runs outside its layer loop.  With one candidate (the track's
+    own hit) the finder must give the fused fit's results (which reaches the
+    exact form through the one-track path of a packed pair), and the FP64
+    finder the oracle's fit (to 1e-9: the 1/pT variance collapses ~170-fold
+    per update in this geometry, which amplifies rounding ~2e5-fold)."""
+    import gpu_util
+    surf = np.array([20.0, 90.0, 160.0, 230.0], np.float32)
+    B = float(np.float32(3.8))
+    pt_min = inputs.pt_min_p2r(B, 230.0, frac=1.0)
+    pt = np.linspace(1.1 * pt_min, 2.5 * pt_min, 1000)
+    ts = inputs.generate(inputs.MODE_R, pt.size, seed=32, surf=surf, pt=pt)
+    cs = inputs.CandidateSet(ts.hpos[:, None], ts.hcov[:, None],
+                             np.zeros((ts.nlayer, ts.n), np.int32))
+    ref_fit = gpu_util.run([ts])
+    f = fit.Fitter(fit.Geometry(B, surf), None)
+    try:
+        got, st = _find(f, ts, cs, np.float32, gate=1e30)
+    finally:
+        f.close()
+    assert (got["chosen"] == 0).all() and (got["status"] == 0).all()
+    assert st["iterations"] == ref_fit["sync"]["iterations"]
+    for k in ("par", "cov", "chi2"):
+        a, b = got[k], ref_fit[k][..., :ts.n]
+        scale = np.maximum(np.abs(b), 1e-30 if k != "cov" else 0.0)
+        if k == "cov":  # relative to the scale of each entry, as in parity.py
+            d = np.abs(a - b)
+            dia = np.abs(b[parity.DIAG])
+            for m, (i, j) in enumerate(parity.PAIRS):
+                assert (d[m] <= 1e-6 * np.sqrt(dia[i] * dia[j])).all(), (k, i, j)
+        else:
+            assert (np.abs(a - b) <= 1e-6 * scale + 1e-6).all(), k
+    f = fit.Fitter(fit.Geometry(B, surf, tol=1e-12), None)
+    try:
+        got64, _ = _find(f, ts, cs, np.float64, gate=1e30)
+    finally:
+        f.close()
+    assert (got64["chosen"] == 0).all()
+    parity.check(got64, oracle.fit_set(ts), "FP64 finder, turning tracks", rtol=1e-9,
+                 chi2_abs=1e-10)
+
+
 def test_stopped_tracks_and_argument_errors():
     surf = inputs.surfaces(inputs.MODE_R)
     n = 64

@@ -60,6 +60,180 @@ def test_multi_event_mixed_modes():
     assert g["sync"]["tracks"] == sum(sizes)
 
 
+@pytest.mark.parametrize("start", [fit.FIT_START_CROSSING, fit.FIT_START_LINE],
+                         ids=["crossing", "line"])
+def test_p2r_starts_reach_the_oracles_crossing(start):
+    """Both starts of the path-length iteration end on the oracle's crossing
+    (its exact first root).  From the closed-form crossing the first step
+    confirms convergence; from the straight line it takes a second one."""
+    ts = inputs.generate(inputs.MODE_R, 4097, seed=31)
+    g = gpu_util.run([ts], layers=True, start=start)
+    parity.check(gpu_util.trim(g, 0, ts.n), oracle.fit_set(ts, want_layers=True), f"start {start}")
+    st = g["sync"]
+    per = st["iterations"] / (ts.n * ts.nlayer)
+    print(f"\nstart {start}: {per:.4f} iterations per track-layer")
+    assert st["not_converged"] == 0 and st["no_intersection"] == 0
+    if start == fit.FIT_START_CROSSING:
+        assert per < 1.01
+    else:
+        assert 1.5 < per < 3.0
+
+
+def _path_lengths(start, B, surf, par, q, R):
+    """fit_path_lengths with the given start: (h, iterations), h NaN where the
+    cylinder is not reached."""
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    f = fit.Fitter(fit.Geometry(B, surf, start=start), None)
+    try:
+        h = torch.empty(R.size, device="cuda")
+        it = torch.empty(R.size, dtype=torch.int32, device="cuda")
+        fit.fit_path_lengths(f.h, dev(par), dev(q), dev(R), h, it)
+        return h.cpu().numpy(), it.cpu().numpy()
+    finally:
+        f.close()
+
+
+def _h_bound(R, h_ref):
+    # the iteration's tolerance 1e-6 R plus a few FP32 roundings of h
+    return 1e-6 * R + 8 * 2.0 ** -24 * h_ref
+
+
+def test_p2r_starts_on_strongly_turning_tracks():
+    """Four cylinders 70 cm apart and pT from 1.1 to 2.5 times the reach
+    limit of the outermost: between cylinders the tracks turn by up to 1 rad,
+    beyond the range of the crossing start's series form (|tan| of half the
+    turn <= 1/4), where its exact form takes over.
+
+    (1) The FP32 path-length step alone, from each truth crossing outwards to
+    the next cylinder and, reversed, inwards to the previous one.  The
+    crossing start reaches every cylinder, as the oracle does, at the
+    oracle's root; the straight-line start reaches every outward one but
+    gives up on inward starts whose tangent misses the cylinder.  (2) The
+    whole fit in FP64 matches the oracle with both starts, to 1e-9: with four
+    hits 70 cm apart each update shrinks the 1/pT variance ~170-fold, and the
+    update C - K H C amplifies rounding ~2e5-fold (measured in FP32, where it
+    leaves ~1e-2 relative with either start), so double keeps ~2e-11 of it,
+    not the 1e-11 of the standard workload.  (3) The FP32 fused fit, where a
+    packed pair hands a track that needs the exact crossing to the one-track
+    path: every track is fitted (status 0), its parameters and chi2 within
+    the FP32 tolerances, at one iteration per track-layer from the crossing
+    start; the covariance is not compared, for the reason above."""
+    surf = np.array([20.0, 90.0, 160.0, 230.0], np.float32)
+    B = float(np.float32(3.8))
+    pt_min = inputs.pt_min_p2r(B, 230.0, frac=1.0)
+    pt = np.linspace(1.1 * pt_min, 2.5 * pt_min, 1000)
+    ts = inputs.generate(inputs.MODE_R, pt.size, seed=32, surf=surf, pt=pt, want_truth=True)
+    # (1) states: truth at cylinder l -> cylinder l + 1, and reversed -> cylinder l - 1
+    par, q, R, inward = [], [], [], []
+    for l in range(ts.nlayer):
+        if l + 1 < ts.nlayer:
+            par.append(ts.truth[l])
+            q.append(ts.q)
+            R.append(np.full(ts.n, surf[l + 1]))
+            inward.append(np.zeros(ts.n, bool))
+        if l >= 1:
+            rev = ts.truth[l].copy()
+            rev[4] += np.pi
+            rev[5] = np.pi - rev[5]
+            par.append(rev)
+            q.append(-ts.q)
+            R.append(np.full(ts.n, surf[l - 1]))
+            inward.append(np.ones(ts.n, bool))
+    par = np.concatenate(par, axis=1).astype(np.float32)
+    q = np.concatenate(q).astype(np.int32)
+    R = np.concatenate(R).astype(np.float32)
+    inward = np.concatenate(inward)
+    h_ref, st_ref = oracle.path_lengths(0, B, R.astype(np.float64), q, par.astype(np.float64))
+    assert (st_ref == 0).all()
+    its = {}
+    for start in (fit.FIT_START_CROSSING, fit.FIT_START_LINE):
+        h, it = _path_lengths(start, B, surf, par, q, R)
+        reached = np.isfinite(h)
+        assert reached[~inward].all(), start
+        if start == fit.FIT_START_CROSSING:
+            assert reached.all()
+        assert (np.abs(h - h_ref)[reached] <= _h_bound(R, h_ref)[reached]).all(), start
+        its[start] = np.where(reached, it, -1)
+    both = (its[fit.FIT_START_LINE] >= 0)
+    c, line = its[fit.FIT_START_CROSSING][both], its[fit.FIT_START_LINE][both]
+    print(f"\nturning tracks: {c.mean():.3f} (crossing) vs {line.mean():.3f} (line) iterations; "
+          f"the line start reaches {both.mean():.3f} of the states")
+    assert c.mean() < line.mean()
+    # (2) the FP64 fit in this geometry, both starts
+    import test_gpu_f64 as f64
+    ref = oracle.fit_set(ts)
+    for start in (fit.FIT_START_CROSSING, fit.FIT_START_LINE):
+        f = fit.Fitter(fit.Geometry(B, surf, tol=f64.TOL_F64, start=start), None)
+        try:
+            got, st = f64._run64(f, ts, layers=False)
+            parity.check(got, ref, f"turning tracks f64, start {start}", rtol=1e-9,
+                         chi2_abs=f64.CHI2_ABS_F64)
+            assert st["not_converged"] == 0 and (got["status"] == 0).all()
+        finally:
+            f.close()
+    # (3) the FP32 fused fit, both starts
+    for start in (fit.FIT_START_CROSSING, fit.FIT_START_LINE):
+        g = gpu_util.run([ts], start=start)
+        e = parity.scaled_errors(gpu_util.trim(g, 0, ts.n), ref)
+        assert (g["status"][:ts.n] == 0).all() and g["sync"]["no_intersection"] == 0, start
+        assert e["par"].max() <= 1 and e["chi2"].max() <= 1, start
+        if start == fit.FIT_START_CROSSING:
+            assert g["sync"]["iterations"] <= 1.01 * ts.n * ts.nlayer
+
+
+def test_crossing_start_reach_and_roots_on_random_states():
+    """200k random p2r states (anywhere within r < 250 cm, any direction,
+    pT from 0.5 to 20 GeV, either charge) to random cylinders 5..260 cm: the
+    crossing start decides reachability like the oracle (the circle meets the
+    cylinder or not), on every state whose track circle passes the cylinder
+    by more than 1e-3 R (near-tangent states may go either way in FP32).  Its
+    path lengths match the oracle's roots where the problem is resolvable in
+    FP32: the crossing not grazing (radial slope > 0.1), a turn below 2 rad,
+    R >= 10 cm and |r0 - R| <= 100 cm (so that the tolerance 1e-6 R is above
+    the rounding of the coordinates)."""
+    rng = np.random.default_rng(7)
+    n = 200_000
+    r0 = rng.uniform(0, 250, n)
+    ang = rng.uniform(0, 2 * np.pi, n)
+    par = np.stack([r0 * np.cos(ang), r0 * np.sin(ang), rng.uniform(-50, 50, n),
+                    rng.uniform(0.05, 2.0, n), rng.uniform(-np.pi, np.pi, n),
+                    rng.uniform(0.5, 2.6, n)]).astype(np.float32)
+    q = np.where(rng.random(n) < 0.5, -1, 1).astype(np.int32)
+    R = rng.uniform(5, 260, n).astype(np.float32)
+    B = float(np.float32(3.8))
+    h_ref, st_ref = oracle.path_lengths(0, B, R.astype(np.float64), q, par.astype(np.float64))
+    # circle geometry of each state (centre distance cn, radius rho) and, at the
+    # oracle's crossing, the turn and the radial slope
+    p = par.astype(np.float64)
+    kap = -q * inputs.KA * B * p[3]
+    cx, cy = p[0] - np.sin(p[4]) / kap, p[1] + np.cos(p[4]) / kap
+    cn, rho = np.hypot(cx, cy), 1.0 / np.abs(kap)
+    margin = np.minimum(np.abs(R - (cn + rho)), np.abs(R - np.abs(cn - rho)))
+    u = 0.5 * kap * h_ref
+    chord = 2.0 * np.sin(u) / kap
+    xe, ye = p[0] + chord * np.cos(p[4] + u), p[1] + chord * np.sin(p[4] + u)
+    slope = np.abs(xe * np.cos(p[4] + 2 * u) + ye * np.sin(p[4] + 2 * u)) / R
+    surf = np.array([10.0], np.float32)
+    h, it = _path_lengths(fit.FIT_START_CROSSING, B, surf, par, q, R)
+    reach, reach_ref = np.isfinite(h), st_ref == 0
+    robust = margin > 1e-3 * R
+    assert np.array_equal(reach[robust], reach_ref[robust])
+    assert (reach != reach_ref).sum() <= 20
+    fair = (reach & reach_ref & (slope > 0.1) & (np.abs(kap) * h_ref < 2.0) & (R >= 10)
+            & (np.abs(r0 - R) <= 100))
+    assert fair.sum() > 50_000
+    assert (np.abs(h - h_ref)[fair] <= _h_bound(R, h_ref)[fair]).all()
+    assert (it[fair] >= 10).sum() <= 20  # flagged as not converged
+    print(f"\nrandom states: {reach_ref.sum()} reachable, {(reach != reach_ref).sum()} "
+          f"reach decisions differ; {it[fair].mean():.4f} iterations on {fair.sum()}")
+
+
+def test_bad_start_is_an_argument_error():
+    with pytest.raises(fit.FitError) as e:
+        fit.Fitter(fit.Geometry(3.8, inputs.surfaces(0), start=7), None)
+    assert e.value.code == fit.FIT_ERR_ARG
+
+
 def test_in_place_equals_out_of_place():
     ts = inputs.generate(inputs.MODE_R, 700, seed=3)
     a = gpu_util.run([ts])
