@@ -45,6 +45,17 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # and out 229 B / nlayer).
 FLOPS_P2Z = 489.0
 FLOPS_P2R = 700.0
+# p2r from the straight-line start: 723 flops at its measured 2.007 iterations
+# per track-layer.  With the crossing start's ~22 more flops (its closed form
+# against the straight-line distance) the two counts give ~45 flops per
+# path-length iteration; a kernel that starts on the straight line and takes
+# `it` iterations is counted as FLOPS_P2R_LINE - 45 (2.007 - it).
+FLOPS_P2R_LINE = 723.0
+FLOPS_P2R_ITERATION = 45.0
+
+
+def flops_p2r_line(iterations: float) -> float:
+    return FLOPS_P2R_LINE - FLOPS_P2R_ITERATION * (2.007 - iterations)
 BYTES_TRACK_IN = (6 + 21 + 1) * 4
 BYTES_TRACK_OUT = (6 + 21 + 1 + 1) * 4 + 1
 
@@ -722,7 +733,8 @@ def bench_seed(args, world, rank, local):
     tl = n * NLAYER
     peaks = load_peaks()
     alu_peak = fp32_peak_tflops(peaks["sm_max_mhz"])
-    alu_ach = FLOPS_P2R * tl / (ms / 1e3) / 1e12
+    seeded_flops = flops_p2r_line(res["network"]["iterations_per_track_layer"])
+    alu_ach = seeded_flops * tl / (ms / 1e3) / 1e12
     mlp_flops = 2.0 * 4801  # multiply-adds of the network per track-layer, x 2
     line = {"metric": "track-layer propagate+update/s", "value": res["network"]["value"],
             "unit": "track-layer/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -733,7 +745,7 @@ def bench_seed(args, world, rank, local):
                        "inputs_exceed_l2": True},
             "roofline": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": alu_ach / alu_peak, "traffic": None, "kernel": "fit_seeded_kernel",
-                         "flops_per_track_layer": FLOPS_P2R,
+                         "flops_per_track_layer": seeded_flops,
                          "network_tensor_tflops": mlp_flops * tl / (ms / 1e3) / 1e12},
             "clocks": clk, "gpu_launches": args.steps,
             "plain_fit": res["straight_line"], "seeded_fit": res["network"],
