@@ -925,6 +925,24 @@ def main():
     f.sync(stream)
     f.close()
 
+    # The same p2r launch from the straight-line start (FIT_START_LINE), after
+    # the timed region: what the closed-form crossing start saves.
+    fl = fit.Fitter(fit.Geometry(sets[0].B, sets[0].surf, start=fit.FIT_START_LINE), None,
+                    device=local)
+    for _ in range(args.warmup):
+        fl.run(*dev_in[0], ntrk, [0] * NEVT, out=outs[0], stream=stream)
+    fl.sync(stream)
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0.record(stream)
+    for _ in range(args.steps):
+        fl.run(*dev_in[0], ntrk, [0] * NEVT, out=outs[0], stream=stream)
+    l1.record(stream)
+    torch.cuda.synchronize(dev)
+    st_line = fl.sync(stream)
+    fl.close()
+    line_start = {"kernel_ms": max_over_ranks(world, l0.elapsed_time(l1) / args.steps),
+                  "iterations_per_track_layer": st_line["iterations"] / (args.steps * n * NLAYER)}
+
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": "track-layer/s",
@@ -937,7 +955,8 @@ def main():
                     "path": "one fit_propagate_update_host call per step on page-locked host "
                             "buffers holding both modes (chunked copies in, fit, copies out, "
                             "three streams)"},
-            "gpu_launches": 2 * args.steps, "p2r_iterations_per_track_layer": it_per}
+            "gpu_launches": 2 * args.steps, "p2r_iterations_per_track_layer": it_per,
+            "p2r_straight_line_start": line_start}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sets)
     print(json.dumps(line))
