@@ -398,15 +398,18 @@ int fit_find_tracks_f64(fit_handle* h, const fit_tracks_in_f64* in, const fit_tr
  * structs, layouts and checks; every data pointer in in, out and hits is a
  * host pointer, page-locked for the copies to overlap the kernels -- pageable
  * memory works but serialises).  The library cuts the tracks into chunks of
- * up to 131072 and moves each through one of three device staging sets on
- * one of three internal streams: copy in, fit, copy out, so that one chunk's
- * copies overlap the others' fits (the paper's transfers of Sec. 3.1 and its
- * measurement with them included).  Asynchronous on `stream` like
+ * up to FIT_HOST_CHUNK and moves each through one of three device staging
+ * sets on one of three internal streams: copy in, fit, copy out, so that one
+ * chunk's copies overlap the others' fits (the paper's transfers of Sec. 3.1
+ * and its measurement with them included).  A chunk's rows are 2-D copies of
+ * FIT_HOST_CHUNK x 4 bytes per row; narrower rows cost the copy engine
+ * bandwidth (512 KiB rows moved 186 GB/s where 1 MiB rows move 207).  Asynchronous on `stream` like
  * fit_propagate_update: the host buffers must stay valid and unchanged until
  * the stream passes the call (fit_sync).  The staging (about 1 KiB per track
  * of a chunk and per 20 layers, three times) is allocated on first use and
  * kept by the handle.  Per-chunk results are bit-identical to fit_propagate_update.
  */
+#define FIT_HOST_CHUNK 262144
 int fit_propagate_update_host(fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
                               const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
                               const int32_t* mode, void* stream);

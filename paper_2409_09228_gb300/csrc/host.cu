@@ -19,10 +19,14 @@ using namespace fitimpl;
 
 namespace {
 
-constexpr int64_t kChunk = 131072;  // tracks per chunk (a multiple of 4)
-// Staging sets and streams.  On GB300 (one H2D copy engine at ~211 GB/s),
-// 131072 tracks and 3 sets measured best end to end: 9.3 ms per bench step
-// against 9.6 with 2 sets and 12-14 ms with 65536 or 262144 tracks.
+constexpr int64_t kChunk = FIT_HOST_CHUNK;  // tracks per chunk (a multiple of 4)
+static_assert(kChunk % 4 == 0, "chunks start at multiples of 4 tracks");
+// Staging sets and streams.  On GB300 the host link moves ~211 GB/s H2D
+// whatever the number of streams, but 2-D copies lose bandwidth with narrow
+// rows (~0.3 us per row): 65536-, 131072- and 262144-track chunks move
+// 144, 186 and 207 GB/s.  Measured end to end (bench step, both modes):
+// 262144 tracks with 3 sets 8.14 ms, against 9.29 ms with 131072; larger
+// chunks or a fourth set change nothing.
 constexpr int kSets = 3;
 
 struct HostStage {

@@ -33,6 +33,7 @@ FIT_ST_NONFINITE = 4
 FIT_ST_CHARGE_FLIP = 8
 FIT_START_CROSSING = 0
 FIT_START_LINE = 1
+FIT_HOST_CHUNK = 262144
 FIT_MAX_LAYERS = 64
 
 

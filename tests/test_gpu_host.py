@@ -1,5 +1,5 @@
 """fit_propagate_update_host: the fused fit on host buffers, copied through
-the library's three staging sets in chunks of 131072 tracks.  Its results must
+the library's three staging sets in chunks of FIT_HOST_CHUNK tracks.  Its results must
 be bit-identical to fit_propagate_update on the same data in device memory:
 chunks start at even track indices, so every track meets the same kernel with
 the same pairing."""
@@ -44,7 +44,7 @@ def _np(x, n):
     return (x.numpy() if hasattr(x, "numpy") else np.asarray(x))[..., :n]
 
 
-@pytest.mark.parametrize("nevt,median,pinned", [(40, 9000.0, True), (7, 100.0, False)])
+@pytest.mark.parametrize("nevt,median,pinned", [(60, 9000.0, True), (7, 100.0, False)])
 def test_host_path_is_bit_identical_to_device_path(nevt, median, pinned):
     ev = _events(nevt, 91 + nevt, median)
     n = ev.n
@@ -65,7 +65,7 @@ def test_host_path_is_bit_identical_to_device_path(nevt, median, pinned):
             assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), k
         assert st_host == st_dev
         if pinned:
-            assert n > 2 * 131072  # several chunks, events straddling their edges
+            assert n > 2 * fit.FIT_HOST_CHUNK  # several chunks, events straddling their edges
     finally:
         f.close()
 
