@@ -6,7 +6,8 @@ when the oracle disagrees with something the physics or mathematics fixes:
 * the Lorentz-force equation of motion, integrated here by RK4 (helix);
 * the helix as a rotation about its centre, written here independently;
 * straight-line closed forms (B = 0 or w -> 0): line-plane, line-cylinder;
-* brute-force scan + bisection of r(h) = R (first crossing of a cylinder);
+* brute-force scan + bisection of r(h) = R (first crossing of a cylinder),
+  and its closed form through the tangent of half the turning angle;
 * central finite differences (transport Jacobian, chi2 gradient);
 * Kalman limits: infinite hit error changes nothing, zero hit error snaps the
   measured coordinates onto the hit; the information form
@@ -226,6 +227,60 @@ def pin_path_r_bruteforce(orc):
         assert abs(h - href) < 1e-7 * max(1.0, href), (h, href)
         checked += 1
     assert checked >= 30
+
+
+def _first_crossing_half_angle(p, q, R):
+    """First forward crossing of r = R in closed form, vectorised over states
+    p (6, n): with t = tan(kappa h / 2) the transverse displacement over h is
+    the chord 2 sin(kappa h / 2) / kappa at angle phi + kappa h / 2, so
+    r(h)^2 = R^2 becomes 2 F t^2 + 2 kappa b0 t + kappa^2 c0 / 2 = 0 with b0,
+    t0 the start's components along and across phi, c0 = r0^2 - R^2 and
+    F = 1 + kappa (t0 + kappa c0 / 4).  No real root (X = b0^2 - c0 F < 0):
+    the circle misses the cylinder (NaN).  Each root gives h = 2 atan(t) /
+    kappa modulo a turn; the first crossing is the smaller one in (0, turn]."""
+    x, y, w, phi = p[0], p[1], p[3], p[4]
+    kap = -q * KA * B * w
+    b0 = x * np.cos(phi) + y * np.sin(phi)
+    t0 = y * np.cos(phi) - x * np.sin(phi)
+    c0 = x * x + y * y - R * R
+    F = 1.0 + kap * (t0 + 0.25 * kap * c0)
+    X = b0 * b0 - c0 * F
+    sq = np.sqrt(np.where(X >= 0, X, 0.0))
+    turn = 2 * np.pi / np.abs(kap)
+    best = np.full(x.shape, np.inf)
+    for sign in (1.0, -1.0):
+        hk = 2 * np.arctan2(-0.5 * kap * c0, b0 + sign * sq) / kap
+        hk = hk - np.floor(hk / turn) * turn
+        hk = np.where(hk > 0, hk, hk + turn)
+        best = np.minimum(best, hk)
+    return np.where(X >= 0, best, np.nan)
+
+
+def pin_path_r_half_angle(orc):
+    """20k random p2r states (anywhere in r < 250 cm, any direction, pT 0.3-20
+    GeV, either charge) to random cylinders: the oracle's path length is the
+    half-angle closed form's first crossing, and it reports no intersection
+    exactly where the circle misses the cylinder (states whose circle passes
+    within 1e-6 R of tangency aside)."""
+    rng = np.random.default_rng(23)
+    n = 20000
+    r0, a0 = rng.uniform(0, 250, n), rng.uniform(-np.pi, np.pi, n)
+    p = np.stack([r0 * np.cos(a0), r0 * np.sin(a0), rng.uniform(-50, 50, n),
+                  rng.uniform(0.05, 3.3, n), rng.uniform(-np.pi, np.pi, n),
+                  rng.uniform(0.5, 2.6, n)])
+    q = np.where(rng.random(n) < 0.5, -1, 1).astype(np.int32)
+    R = rng.uniform(5, 260, n)
+    h_ref, st = orc.path_lengths(MODE_R, B, R, q, p)
+    h = _first_crossing_half_angle(p, q, R)
+    kap = -q * KA * B * p[3]
+    cx, cy = p[0] - np.sin(p[4]) / kap, p[1] + np.cos(p[4]) / kap
+    cn, rho = np.hypot(cx, cy), 1 / np.abs(kap)
+    clear = np.minimum(np.abs(R - (cn + rho)), np.abs(R - np.abs(cn - rho))) > 1e-6 * R
+    reach = st == 0
+    assert np.array_equal(reach[clear], np.isfinite(h)[clear])
+    both = reach & np.isfinite(h) & clear
+    assert both.sum() > 8000 and (~reach & clear).sum() > 4000
+    assert (np.abs(h_ref - h)[both] <= 1e-9 * np.maximum(h[both], 1.0)).all()
 
 
 def _scales(p):
@@ -543,6 +598,7 @@ ALL_PINS = [
     pin_straight_line_surfaces,
     pin_landing,
     pin_path_r_bruteforce,
+    pin_path_r_half_angle,
     pin_jacobian_fd,
     pin_update_limits,
     pin_update_information_form,
