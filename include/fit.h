@@ -208,10 +208,13 @@ int fit_propagate_update_noalloc(const fit_config* cfg_r, const fit_config* cfg_
  * those of fit_propagate_update on the same events.
  */
 typedef struct {
-  int threads_per_block; /* 64 or 128 (two tracks per thread) */
+  int threads_per_block; /* 32, 64 or 128 */
   int blocks_per_sm;     /* grid = blocks_per_sm x SM count; 0 = as many as fit */
   int persistent;        /* 1: one persistent launch; 0: one launch per run of
                             same-mode events (fit_propagate_update's form) */
+  int tracks_per_thread; /* 2 (or 0, a zeroed struct): two tracks per thread in
+                            packed f32x2 instructions; 1: one track per thread
+                            (persistent form only) */
 } fit_launch_config;
 
 typedef struct {
@@ -227,8 +230,8 @@ typedef struct fit_plan fit_plan;
 
 /*
  * fit_plan_create: a plan for nevt events (ntrk, mode: HOST arrays, copied).
- * cfg may be NULL (persistent, 128 threads per block, as many blocks per SM
- * as fit).  The plan allocates its work-item table and a counter on the
+ * cfg may be NULL (persistent, 128 threads per block, two tracks per thread,
+ * as many blocks per SM as fit).  The plan allocates its work-item table and a counter on the
  * handle's device.  Errors: FIT_ERR_ARG, FIT_ERR_NOMEM, FIT_ERR_CUDA.
  */
 int fit_plan_create(fit_handle* h, int nevt, const int64_t* ntrk, const int32_t* mode, int nlayer,
@@ -244,8 +247,9 @@ int fit_plan_run(fit_plan* plan, const fit_tracks_in* in, const fit_tracks_out* 
 
 /*
  * fit_plan_tune: the autotuner.  Times every candidate launch shape (persistent
- * with 64 or 128 threads per block at each resident-block count, and the
- * per-segment form) on these buffers -- out must not alias in, it is written --
+ * with two tracks per thread and 32, 64 or 128 threads per block, or one track
+ * per thread and 64 or 128 threads per block, each at every resident-block
+ * count; and the per-segment form) on these buffers -- out must not alias in, it is written --
  * and keeps the fastest.  A shape found before for the same device, depth and
  * event-size histogram (in this process, or in the text file cache_path if not
  * NULL) is reused without measuring; new results are appended to cache_path.

@@ -2,9 +2,10 @@
 // mixed surface types (p2r / p2z) in one persistent launch, replayed from a
 // CUDA graph, with a launch-shape autotuner (fit_plan_* in fit.h).
 //
-// Work items are tiles of one event: 2 x threads_per_block consecutive tracks
-// (two per thread), never crossing an event, so each item has one surface
-// type and the branch on it is uniform across the block.  Blocks pull items
+// Work items are tiles of one event: threads_per_block x tracks_per_thread
+// consecutive tracks (two per thread in packed f32x2 instructions, or one),
+// never crossing an event, so each item has one surface type and the branch
+// on it is uniform across the block.  Blocks pull items
 // from an atomic counter until none is left (dynamic load balance across
 // uneven events and the cheaper p2z items).
 #include <cuda_runtime.h>
@@ -25,7 +26,7 @@ namespace fitimpl {
 namespace {
 
 struct WorkItem {
-  int64_t first;       // track of the item's first pair (even)
+  int64_t first;       // the item's first track (even with two per thread)
   int64_t begin, end;  // the event's track range
   int32_t mode;
   int32_t event;
@@ -39,11 +40,12 @@ struct BatchArgs {
   unsigned* work_counter;
 };
 
-// At least 384 resident threads per SM (3 blocks of 128, 6 of 64), as for
-// fit_fused_kernel's p2r: left free, the compiler takes ~190 registers and
-// only 2 blocks of 128 fit.
-template <int BLK>
-__global__ void __launch_bounds__(BLK, 384 / BLK)
+// TPT tracks per thread.  Two: at least 384 resident threads per SM (3
+// blocks of 128, 6 of 64, 12 of 32), as for fit_fused_kernel's p2r: left
+// free, the compiler takes ~190 registers and only 2 blocks of 128 fit.
+// One: at least 512 (128 registers).
+template <int BLK, int TPT>
+__global__ void __launch_bounds__(BLK, (TPT == 2 ? 384 : 512) / BLK)
     fit_batched_kernel(const __grid_constant__ BatchArgs b) {
   __shared__ int s_item;
   for (;;) {
@@ -53,6 +55,22 @@ __global__ void __launch_bounds__(BLK, 384 / BLK)
     const int it = s_item;
     if (it >= b.nitems) return;
     const WorkItem w = b.items[it];
+    if constexpr (TPT == 1) {
+      const int64_t t = w.first + (int64_t)threadIdx.x;
+      if (t < w.end) {
+        unsigned st = 0u, iters = 0u;
+        State<float> s;
+        load_state(b.a, t, s);
+        if (w.mode == FIT_MODE_Z) {
+          finish_one<FIT_MODE_Z>(b.a, b.geo[FIT_MODE_Z], t, 0, s, st, iters, true);
+        } else {
+          finish_one<FIT_MODE_R>(b.a, b.geo[FIT_MODE_R], t, 0, s, st, iters, true);
+          count_iterations(iters, &b.a.counters[4]);
+        }
+        if (st) count_status(st, b.a.counters);
+      }
+      continue;
+    }
     const int64_t t = w.first + 2 * (int64_t)threadIdx.x;
     if (t < w.end) {
       unsigned st[2] = {0u, 0u}, iters[2] = {0u, 0u};
@@ -82,14 +100,26 @@ __global__ void __launch_bounds__(kBlock, MODE == FIT_MODE_Z ? 4 : 3)
   if (MODE == FIT_MODE_R) count_iterations(iters[0] + iters[1], &a.counters[4]);
 }
 
-int max_blocks_per_sm(int tpb) {
+int tracks_per_thread(const fit_launch_config& c) { return c.tracks_per_thread == 1 ? 1 : 2; }
+
+// The batched kernel for a launch shape, or NULL for a shape not compiled.
+const void* batched_kernel(int tpb, int tpt) {
+  if (tpt == 2) {
+    if (tpb == 32) return (const void*)fit_batched_kernel<32, 2>;
+    if (tpb == 64) return (const void*)fit_batched_kernel<64, 2>;
+    if (tpb == 128) return (const void*)fit_batched_kernel<128, 2>;
+  } else {
+    if (tpb == 64) return (const void*)fit_batched_kernel<64, 1>;
+    if (tpb == 128) return (const void*)fit_batched_kernel<128, 1>;
+  }
+  return nullptr;
+}
+
+int max_blocks_per_sm(int tpb, int tpt) {
+  const void* k = batched_kernel(tpb, tpt);
   int n = 0;
-  cudaError_t e = cudaSuccess;
-  if (tpb == 64)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fit_batched_kernel<64>, 64, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fit_batched_kernel<128>, 128, 0);
-  return e == cudaSuccess ? n : 0;
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, tpb, 0) != cudaSuccess) return 0;
+  return n;
 }
 
 std::string cache_key(int device, int nlayer, const std::vector<int64_t>& ntrk,
@@ -109,7 +139,7 @@ std::string cache_key(int device, int nlayer, const std::vector<int64_t>& ntrk,
     hist[mode[e]][b]++;
     tracks[mode[e]] += ntrk[e];
   }
-  std::string k = name + ";nlayer=" + std::to_string(nlayer) + ";tracks=" +
+  std::string k = name + ";v2;nlayer=" + std::to_string(nlayer) + ";tracks=" +
                   std::to_string(tracks[0]) + "," + std::to_string(tracks[1]) + ";hist=";
   for (int m = 0; m < 2; ++m)
     for (int b = 0; b < 64; ++b)
@@ -132,7 +162,8 @@ bool read_cache(const char* path, const std::string& key, fit_launch_config* cfg
     *tab = 0;
     if (key != line) continue;
     fit_launch_config c{};
-    if (std::sscanf(tab + 1, "%d %d %d", &c.threads_per_block, &c.blocks_per_sm, &c.persistent) == 3) {
+    if (std::sscanf(tab + 1, "%d %d %d %d", &c.threads_per_block, &c.blocks_per_sm, &c.persistent,
+                    &c.tracks_per_thread) == 4) {
       *cfg = c;  // the last matching line wins
       found = true;
     }
@@ -145,8 +176,8 @@ void append_cache(const char* path, const std::string& key, const fit_launch_con
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s\t%d %d %d %.4f\n", key.c_str(), c.threads_per_block, c.blocks_per_sm,
-               c.persistent, ms);
+  std::fprintf(f, "%s\t%d %d %d %d %.4f\n", key.c_str(), c.threads_per_block, c.blocks_per_sm,
+               c.persistent, tracks_per_thread(c), ms);
   std::fclose(f);
 }
 
@@ -161,11 +192,12 @@ struct fit_plan {
   std::vector<int64_t> ntrk;
   std::vector<int32_t> mode;
   int64_t total = 0;
-  fit_launch_config cfg{128, 0, 1};
+  fit_launch_config cfg{128, 0, 1, 2};
   int sms = 0;
   WorkItem* d_items = nullptr;
   int nitems = 0;
-  int items_tpb = 0;
+  int items_tile = 0;  // tracks per work item of the current table
+  int items_tpt = 0;
   unsigned* d_work = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -178,18 +210,20 @@ struct fit_plan {
 
 namespace {
 
-int build_items(fit_plan* p, int tpb) {
-  if (p->items_tpb == tpb && p->d_items) return FIT_OK;
+// Work items of tpb x tpt tracks.  With two tracks per thread an item starts
+// at an even track (packed loads are 8-byte aligned), so an event's first
+// item may begin one track early; the kernel skips tracks outside the event.
+int build_items(fit_plan* p, int tpb, int tpt) {
+  if (p->items_tile == tpb * tpt && p->items_tpt == tpt && p->d_items) return FIT_OK;
   std::vector<WorkItem> items;
   int64_t start = 0;
   for (size_t e = 0; e < p->ntrk.size(); ++e) {
     const int64_t begin = start, end = start + p->ntrk[e];
     start = end;
     if (end == begin) continue;
-    const int64_t first = begin & ~int64_t(1);
-    const int64_t npairs = (end - first + 1) / 2;
-    for (int64_t k = 0; k < npairs; k += tpb)
-      items.push_back({first + 2 * k, begin, end, p->mode[e], (int32_t)e});
+    const int64_t first = tpt == 2 ? begin & ~int64_t(1) : begin;
+    for (int64_t t = first; t < end; t += (int64_t)tpb * tpt)
+      items.push_back({t, begin, end, p->mode[e], (int32_t)e});
   }
   if (items.size() > 0x7fffffff) return fail(FIT_ERR_ARG, "fit_plan: too many work items");
   DeviceGuard g(p->h->device);
@@ -200,7 +234,8 @@ int build_items(fit_plan* p, int tpb) {
   }
   p->d_items = nullptr;
   p->nitems = (int)items.size();
-  p->items_tpb = tpb;
+  p->items_tile = tpb * tpt;
+  p->items_tpt = tpt;
   if (items.empty()) return FIT_OK;
   cudaError_t e = cudaMalloc(&p->d_items, items.size() * sizeof(WorkItem));
   if (e != cudaSuccess) return fail(FIT_ERR_NOMEM, "fit_plan: cudaMalloc of the work items");
@@ -223,10 +258,19 @@ int issue(fit_plan* p, const FitArgs& base, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(p->d_work, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return cuda_fail(e, "fit_plan: work counter reset");
     const unsigned grid = (unsigned)std::max(1, p->cfg.blocks_per_sm * p->sms);
-    if (p->cfg.threads_per_block == 64)
-      fit_batched_kernel<64><<<grid, 64, 0, s>>>(b);
-    else
-      fit_batched_kernel<128><<<grid, 128, 0, s>>>(b);
+    const int tpb = p->cfg.threads_per_block;
+    if (tracks_per_thread(p->cfg) == 1) {
+      if (tpb == 64)
+        fit_batched_kernel<64, 1><<<grid, 64, 0, s>>>(b);
+      else
+        fit_batched_kernel<128, 1><<<grid, 128, 0, s>>>(b);
+    } else if (tpb == 32) {
+      fit_batched_kernel<32, 2><<<grid, 32, 0, s>>>(b);
+    } else if (tpb == 64) {
+      fit_batched_kernel<64, 2><<<grid, 64, 0, s>>>(b);
+    } else {
+      fit_batched_kernel<128, 2><<<grid, 128, 0, s>>>(b);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fit_plan: launch");
     return FIT_OK;
@@ -274,7 +318,7 @@ int run_graph(fit_plan* p, const fit_tracks_in* in, const fit_tracks_out* out,
                     std::memcmp(lds, p->key_ld, sizeof(lds)) == 0;
   if (!same) {
     drop_graph(p);
-    int rc = build_items(p, p->cfg.threads_per_block);
+    int rc = build_items(p, p->cfg.threads_per_block, tracks_per_thread(p->cfg));
     if (rc != FIT_OK) return rc;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
@@ -328,9 +372,11 @@ int fit_plan_create(fit_handle* h, int nevt, const int64_t* ntrk, const int32_t*
       return fail(FIT_ERR_ARG, "fit_plan_create: nlayer differs from the configured one");
     total += ntrk[e];
   }
-  if (cfg && ((cfg->threads_per_block != 64 && cfg->threads_per_block != 128) ||
-              cfg->blocks_per_sm < 0))
-    return fail(FIT_ERR_ARG, "fit_plan_create: threads_per_block must be 64 or 128");
+  if (cfg && (cfg->tracks_per_thread < 0 || cfg->tracks_per_thread > 2 || cfg->blocks_per_sm < 0 ||
+              !batched_kernel(cfg->threads_per_block, tracks_per_thread(*cfg)) ||
+              (!cfg->persistent && tracks_per_thread(*cfg) != 2)))
+    return fail(FIT_ERR_ARG, "fit_plan_create: threads_per_block must be 32, 64 or 128 with two "
+                             "tracks per thread, 64 or 128 with one (persistent only)");
   DeviceGuard g(h->device);
   fit_plan* p = new fit_plan();
   p->h = h;
@@ -346,7 +392,9 @@ int fit_plan_create(fit_handle* h, int nevt, const int64_t* ntrk, const int32_t*
   }
   p->sms = prop.multiProcessorCount;
   if (cfg) p->cfg = *cfg;
-  if (p->cfg.blocks_per_sm == 0) p->cfg.blocks_per_sm = max_blocks_per_sm(p->cfg.threads_per_block);
+  p->cfg.tracks_per_thread = tracks_per_thread(p->cfg);
+  if (p->cfg.blocks_per_sm == 0)
+    p->cfg.blocks_per_sm = max_blocks_per_sm(p->cfg.threads_per_block, p->cfg.tracks_per_thread);
   if (p->cfg.blocks_per_sm <= 0) p->cfg.blocks_per_sm = 1;
   e = cudaMalloc(&p->d_work, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_tune_counters, kCounters * sizeof(unsigned long long));
@@ -355,7 +403,7 @@ int fit_plan_create(fit_handle* h, int nevt, const int64_t* ntrk, const int32_t*
     fit_plan_destroy(p);
     return fail(FIT_ERR_NOMEM, std::string("fit_plan_create: ") + cudaGetErrorString(e));
   }
-  int rc = build_items(p, p->cfg.threads_per_block);
+  int rc = build_items(p, p->cfg.threads_per_block, p->cfg.tracks_per_thread);
   if (rc != FIT_OK) {
     fit_plan_destroy(p);
     return rc;
@@ -407,14 +455,17 @@ int fit_plan_tune(fit_plan* p, const fit_tracks_in* in, const fit_tracks_out* ou
     p->best_ms = 0.f;
     return FIT_OK;
   }
-  // Candidates: persistent with 64 or 128 threads per block at every
-  // resident-block count, and the one-launch-per-segment form.
+  // Candidates: persistent with two tracks per thread and 32, 64 or 128
+  // threads per block, or one track per thread and 64 or 128, each at every
+  // resident-block count; and the one-launch-per-segment form.
   std::vector<fit_launch_config> cands;
-  for (int tpb : {64, 128}) {
-    const int maxb = max_blocks_per_sm(tpb);
-    for (int b = 1; b <= maxb; ++b) cands.push_back({tpb, b, 1});
-  }
-  cands.push_back({128, 0, 0});
+  for (int tpt : {2, 1})
+    for (int tpb : {32, 64, 128}) {
+      if (!batched_kernel(tpb, tpt)) continue;
+      const int maxb = max_blocks_per_sm(tpb, tpt);
+      for (int b = 1; b <= maxb; ++b) cands.push_back({tpb, b, 1, tpt});
+    }
+  cands.push_back({128, 0, 0, 2});
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(FIT_ERR_CUDA, "fit_plan_tune: cudaEventCreate");
@@ -461,10 +512,12 @@ int fit_plan_get_info(const fit_plan* p, fit_plan_info* info) {
   info->config = p->cfg;
   info->tracks = p->total;
   int64_t items = 0, start = 0;
-  const int tpb = p->cfg.threads_per_block;
+  const int tpt = tracks_per_thread(p->cfg);
+  const int64_t tile = (int64_t)p->cfg.threads_per_block * tpt;
   for (size_t e = 0; e < p->ntrk.size(); ++e) {
     const int64_t end = start + p->ntrk[e];
-    if (end > start) items += ((end - (start & ~int64_t(1)) + 1) / 2 + tpb - 1) / tpb;
+    const int64_t first = tpt == 2 ? start & ~int64_t(1) : start;
+    if (end > start) items += (end - first + tile - 1) / tile;
     start = end;
   }
   info->items = (int32_t)items;

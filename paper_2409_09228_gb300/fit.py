@@ -72,7 +72,7 @@ class fit_status(ctypes.Structure):
 
 class fit_launch_config(ctypes.Structure):
     _fields_ = [("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("persistent", ctypes.c_int)]
+                ("persistent", ctypes.c_int), ("tracks_per_thread", ctypes.c_int)]
 
 
 class fit_plan_info(ctypes.Structure):
@@ -430,11 +430,12 @@ def _buffers(par_in, cov_in, q_in, hpos, hcov, par_out, cov_out, q_out, chi2, ch
 
 def fit_plan_create(h: int, ntrk: Sequence[int], mode: Sequence[int], nlayer: int,
                     threads_per_block: int = 128, blocks_per_sm: int = 0,
-                    persistent: bool = True) -> int:
+                    persistent: bool = True, tracks_per_thread: int = 2) -> int:
     """A plan for the batched persistent form (see fit.h)."""
     nt = np.ascontiguousarray(ntrk, dtype=np.int64)
     md = np.ascontiguousarray(mode, dtype=np.int32)
-    cfg = fit_launch_config(threads_per_block, blocks_per_sm, int(persistent))
+    cfg = fit_launch_config(threads_per_block, blocks_per_sm, int(persistent),
+                            int(tracks_per_thread))
     p = ctypes.c_void_p()
     _check(load().fit_plan_create(ctypes.c_void_p(h), len(nt),
                                   nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
@@ -466,7 +467,8 @@ def fit_plan_get_info(plan: int) -> dict:
     _check(load().fit_plan_get_info(ctypes.c_void_p(plan), ctypes.byref(info)))
     c = info.config
     return {"threads_per_block": c.threads_per_block, "blocks_per_sm": c.blocks_per_sm,
-            "persistent": bool(c.persistent), "tracks": info.tracks, "items": info.items,
+            "persistent": bool(c.persistent), "tracks_per_thread": c.tracks_per_thread,
+            "tracks": info.tracks, "items": info.items,
             "tuned": info.tuned, "best_ms": info.best_ms}
 
 

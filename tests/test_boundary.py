@@ -81,7 +81,8 @@ def test_struct_layouts_match_header():
 
 
 def test_plan_struct_layouts():
-    assert ctypes.sizeof(fit.fit_launch_config) == 12
+    assert ctypes.sizeof(fit.fit_launch_config) == 16
+    assert fit.fit_plan_info.tracks.offset == 16
     assert ctypes.sizeof(fit.fit_plan_info) == 40
     assert ctypes.sizeof(fit.fit_candidates) == 32
     assert ctypes.sizeof(fit.fit_mlp_train_config) == 40

@@ -90,20 +90,26 @@ def test_plan_matches_oracle_and_segments():
         f.close()
 
 
-@pytest.mark.parametrize("tpb,bps,persistent", [(64, 1, 1), (64, 6, 1), (128, 1, 1), (128, 3, 1),
-                                                (128, 0, 0)])
-def test_every_launch_shape(tpb, bps, persistent):
+@pytest.mark.parametrize("tpb,bps,persistent,tpt", [(64, 1, 1, 2), (64, 6, 1, 2), (128, 1, 1, 2),
+                                                    (128, 3, 1, 2), (32, 12, 1, 2), (32, 1, 1, 2),
+                                                    (128, 0, 0, 2), (64, 0, 1, 1),
+                                                    (128, 2, 1, 1)])
+def test_every_launch_shape(tpb, bps, persistent, tpt):
     ev = _events(40, seed=41)
     ld, dev_in = _device(ev)
     f = fit.Fitter(*_geoms(ev))
     plan = fit.fit_plan_create(f.h, ev.ntrk, ev.mode, 20, threads_per_block=tpb,
-                               blocks_per_sm=bps, persistent=bool(persistent))
+                               blocks_per_sm=bps, persistent=bool(persistent),
+                               tracks_per_thread=tpt)
     try:
+        info = fit.fit_plan_get_info(plan)
+        assert info["tracks_per_thread"] == tpt and info["threads_per_block"] == tpb
         out = _outputs(f, ev, ld)
         fit.fit_plan_run(plan, *dev_in, par_out=out["par"], cov_out=out["cov"], q_out=out["q"],
                          chi2=out["chi2"], status=out["status"])
-        f.sync()
-        _check_against_oracle(ev, _fetch(out, ev.n), f"shape {tpb},{bps},{persistent}")
+        st = f.sync()
+        assert st["tracks"] == ev.n
+        _check_against_oracle(ev, _fetch(out, ev.n), f"shape {tpb},{bps},{persistent},{tpt}")
     finally:
         fit.fit_plan_destroy(plan)
         f.close()
@@ -127,7 +133,7 @@ def test_tune_and_cache(tmp_path):
         assert f.sync()["tracks"] == 0  # the tuning runs are not counted
         info2 = fit.fit_plan_tune(p2, *dev_in, cache_path=cache, **bufs)
         assert info2["tuned"] == 2
-        for k in ("threads_per_block", "blocks_per_sm", "persistent"):
+        for k in ("threads_per_block", "blocks_per_sm", "persistent", "tracks_per_thread"):
             assert info2[k] == info[k]
         fit.fit_plan_run(p2, *dev_in, **bufs)
         f.sync()
@@ -154,6 +160,12 @@ def test_plan_argument_errors():
             fit.fit_plan_create(f.h, [10], [0], 19)  # nlayer differs
         with pytest.raises(fit.FitError):
             fit.fit_plan_create(f.h, [10], [0], 20, threads_per_block=96)
+        with pytest.raises(fit.FitError):  # one track per thread: 64 or 128 threads
+            fit.fit_plan_create(f.h, [10], [0], 20, threads_per_block=32, tracks_per_thread=1)
+        with pytest.raises(fit.FitError):  # ... and persistent only
+            fit.fit_plan_create(f.h, [10], [0], 20, persistent=False, tracks_per_thread=1)
+        with pytest.raises(fit.FitError):
+            fit.fit_plan_create(f.h, [10], [0], 20, tracks_per_thread=3)
     finally:
         f.close()
 
