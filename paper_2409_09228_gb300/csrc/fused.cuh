@@ -108,9 +108,10 @@ __device__ __forceinline__ void store_state(const FitArgs& a, int64_t t, const S
 // The fused layer loop (paper Sec. 3.1: propagate to the next layer, update
 // with its hit) for the lanes of s, tracks t, t+1, ..., from layer l0.
 // MODE selects the surface type at compile time.  Returns the layer whose
-// surface some live lane cannot reach (its propagation is not applied), or
-// nlayer.  A lane whose update turns non-finite stops (alive false); its
-// later per-layer chi2 entries are 0.
+// surface some live lane cannot reach (its propagation is not applied), the
+// layer after one where a packed lane turned non-finite, or nlayer.  A lane
+// whose update turns non-finite stops (alive false); its later per-layer
+// chi2 entries are 0.
 template <int MODE, class T, int L = 0>
 __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int64_t t, int l0,
                                           State<T>& s,
@@ -157,6 +158,13 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
           fitk::st(a.chi2_layer + ix<L>(r, t, a.ld_out, a.nlayer), T(0.f));
       return a.nlayer;
     }
+    // A packed lane that turned non-finite would fail every later
+    // propagation, and a propagation that fails for any lane is applied to
+    // none: the pair splits at the next layer, where the live track goes on
+    // alone and the dead one is only stored.
+    if constexpr (Lanes<T>::n > 1) {
+      if (!fitk::all(alive)) return l + 1;
+    }
   }
   return a.nlayer;
 }
@@ -175,6 +183,8 @@ __device__ __forceinline__ void finish_one(const FitArgs& a, const Geo& geo, int
       if (a.chi2_layer)
         for (int r = l; r < a.nlayer; ++r) a.chi2_layer[ix<L>(r, t, a.ld_out, a.nlayer)] = 0.f;
     }
+  } else if (a.chi2_layer) {  // stopped earlier: no later layer adds to chi2
+    for (int r = l0; r < a.nlayer; ++r) a.chi2_layer[ix<L>(r, t, a.ld_out, a.nlayer)] = 0.f;
   }
   store_state<L>(a, t, s, st1);
   st = st1[0];

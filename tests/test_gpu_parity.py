@@ -234,6 +234,59 @@ def test_bad_start_is_an_argument_error():
     assert e.value.code == fit.FIT_ERR_ARG
 
 
+@pytest.mark.parametrize("mode", [inputs.MODE_R, inputs.MODE_Z], ids=["p2r", "p2z"])
+def test_charge_flip_matches_oracle(mode):
+    """Seeds with the wrong charge and a loose 1/pT (sigma_w = 0.1 / GeV
+    against w = 0.05 / GeV): the first update drives w through zero, and the
+    fit flips q and the sign of w with row and column 3 of C (reading R8).
+    Every track flips, on the GPU as in the oracle, and ends where the
+    oracle's does."""
+    n = 2000
+    ts = inputs.generate(mode, n, seed=61 + mode, pt=np.full(n, 20.0))
+    ts.q = (-ts.q).astype(np.int32)
+    ts.cov0[9] = np.float32(0.1 ** 2)  # (w, w)
+    g = gpu_util.run([ts])
+    r = oracle.fit_set(ts)
+    assert (r["status"] == fit.FIT_ST_CHARGE_FLIP).all()
+    assert np.array_equal(g["status"][:n], r["status"])
+    assert g["sync"]["charge_flip"] == n
+    assert np.array_equal(g["q"][:n], r["q"]) and (r["q"] == -ts.q).all()
+    gs = gpu_util.trim(g, 0, n)
+    gs["status"] = np.zeros(n, np.uint8)
+    rs = dict(r, status=np.zeros(n, np.uint8))
+    parity.check(gs, rs, f"charge flip, mode {mode}")
+
+
+@pytest.mark.parametrize("mode", [inputs.MODE_R, inputs.MODE_Z], ids=["p2r", "p2z"])
+def test_nonfinite_track_leaves_its_pair_alone(mode):
+    """A NaN hit on layer 5 of every seventh track (both positions of a
+    two-track pair): those tracks stop with FIT_ST_NONFINITE, their per-layer
+    chi2 from that layer on is 0, and every other track, the partners of the
+    bad ones included, fits like the oracle."""
+    n = 1000
+    ts = inputs.generate(mode, n, seed=71 + mode)
+    bad = np.arange(0, n, 7)
+    ts.hpos[5, 0, bad] = np.nan
+    g = gpu_util.run([ts], layers=True)
+    r = oracle.fit_set(ts, want_layers=True)
+    good = np.ones(n, bool)
+    good[bad] = False
+    assert (g["status"][:n][bad] & fit.FIT_ST_NONFINITE).all()
+    assert (r["status"][bad] & fit.FIT_ST_NONFINITE).all()
+    assert (g["status"][:n][good] == 0).all() and (r["status"][good] == 0).all()
+    assert g["sync"]["nonfinite"] == bad.size
+    assert (g["chi2_layer"][5:, bad] == 0).all()
+    s = parity.check(gpu_util.trim(g, 0, n), r, f"partners of non-finite tracks, mode {mode}")
+    assert s["compared"] == good.sum()
+    # per-layer chi2 of the good tracks too, the partners' in particular
+    partners = np.unique(np.concatenate([bad ^ 1]))
+    partners = partners[(partners < n) & good[np.minimum(partners, n - 1)]]
+    d = np.abs(g["chi2_layer"][:, partners] - r["chi2_layer"][:, partners])
+    tol = parity.RTOL * r["chi2_layer"][:, partners] + parity.CHI2_ABS * np.sqrt(
+        r["chi2_layer"][:, partners] / ts.nlayer)
+    assert (d <= tol + 1e-6).all()
+
+
 def test_in_place_equals_out_of_place():
     ts = inputs.generate(inputs.MODE_R, 700, seed=3)
     a = gpu_util.run([ts])
