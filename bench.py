@@ -85,7 +85,8 @@ def fp32_peak_tflops(mhz: float) -> float:
 
 # The sources fit_fused_kernel is compiled from (and the constants it takes
 # from include/fit.h); the DRAM traffic committed under profiles/ holds only
-# while they hash to the value recorded there.
+# while their code (comments and layout aside) hashes to the value recorded
+# there.
 FUSED_SOURCES = ("paper_2409_09228_gb300/csrc/fit.cu",
                  "paper_2409_09228_gb300/csrc/fused.cuh",
                  "paper_2409_09228_gb300/csrc/track_math.cuh",
@@ -93,11 +94,36 @@ FUSED_SOURCES = ("paper_2409_09228_gb300/csrc/fit.cu",
                  "paper_2409_09228_gb300/csrc/internal.h")
 
 
+def code_only(text: str) -> str:
+    """C++ source without its comments and with whitespace runs collapsed, so
+    that editing a comment or re-wrapping a line keeps the hash."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":  # a literal: copied up to its closing quote
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for name in FUSED_SOURCES:
-        with open(os.path.join(ROOT, name), "rb") as f:
-            h.update(name.encode() + f.read())
+        with open(os.path.join(ROOT, name)) as f:
+            h.update(name.encode() + code_only(f.read()).encode())
     with open(os.path.join(ROOT, "include", "fit.h")) as f:
         h.update("".join(l for l in f if l.startswith("#define FIT_")).encode())
     return h.hexdigest()[:16]

@@ -400,6 +400,20 @@ __device__ __forceinline__ typename Lanes<T>::M crossing_start(T x, T y, T cph, 
   }
 }
 
+// Where path_r starts when line_start is not set.  kAuto: the closed-form
+// crossing (crossing_start), in its exact form where a one-lane type needs it.
+// kFast: the series form only; a lane that needs the exact form is returned
+// as failing, so that the caller can rerun the surface with kGiven from
+// crossing_exact outside its hot loop (a call or the exact form's code inside
+// that loop slowed the memory-bound finder by 20 %).  kGiven: h_given.
+enum class Start { kAuto, kFast, kGiven };
+
+// The helix quantities of path_r's last evaluation.
+template <class T>
+struct PathR {
+  T h, d, u, s, cu, cm, sm, px, py, c1, s1;
+};
+
 // Path length to the cylinder r = R by straight-line steps along the current
 // direction: from a start h, repeatedly the helix at h and a straight step
 // along its direction to the circle, until a step is below tol_abs.  With
@@ -409,24 +423,11 @@ __device__ __forceinline__ typename Lanes<T>::M crossing_start(T x, T y, T cph, 
 // start is the closed-form crossing (crossing_start), which decides
 // reachability exactly, and one evaluation confirms it.  Returns the mask of
 // lanes that cannot reach the cylinder (the other outputs are then
-// meaningless); with packed lanes also those that need the one-lane form of
-// the crossing start.  On return h is the path length;
+// meaningless); with packed lanes, and with Start::kFast, also those that
+// need the exact form of the crossing start.  On return h is the path length;
 // the helix quantities (u, s, cu, cm, sm, px, py, c1, s1) are those of the
 // last evaluation, at h - d.  iters[i] counts lane i's iterations; notconv
 // marks lanes that reached max_iter.
-// Where path_r starts when line_start is not set.  kAuto: the closed-form
-// crossing (crossing_start), in its exact form where a one-lane type needs it.
-// kFast: the series form only; a lane that needs the exact form is returned
-// as failing, so that the caller can rerun the surface with kGiven from
-// crossing_exact outside its hot loop (a call or the exact form's code inside
-// that loop slowed the memory-bound finder by 20 %).  kGiven: h_given.
-enum class Start { kAuto, kFast, kGiven };
-
-template <class T>
-struct PathR {
-  T h, d, u, s, cu, cm, sm, px, py, c1, s1;
-};
-
 //
 // SEEDED: gseed is the learned seed's output g (mlp.cuh); the iteration starts
 // at h_line + g kappa h_line^2 / 2 instead of the straight-line distance
