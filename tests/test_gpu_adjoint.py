@@ -174,3 +174,27 @@ def test_full_size_adjoint_sampled():
         _assert_close(gp, ref["g_par0"], scale[None, :], "full-size initial-parameter gradient")
     finally:
         f.close()
+
+
+def test_both_p2r_starts_give_the_same_gradient():
+    """The path length is treated as the implicit function of the state that
+    the Jacobian holds, so where the iteration starts (the closed-form
+    crossing or the straight line) changes nothing beyond its tolerance:
+    the two gradients agree component by component within the tolerance
+    against the oracle."""
+    ts = inputs.generate(inputs.MODE_R, 1000, seed=81)
+    ld = gpu_util.pad_ld(ts.n)
+    d = [gpu_util.to_dev(a, ld) for a in (ts.par0, ts.cov0, ts.q, ts.hpos, ts.hcov)]
+    grads = {}
+    for start in (fit.FIT_START_CROSSING, fit.FIT_START_LINE):
+        f = fit.Fitter(fit.Geometry(ts.B, ts.surf, start=start), None)
+        try:
+            _, gh, gp = _gpu_grad(f, ts, ld, d)
+        finally:
+            f.close()
+        grads[start] = (gh, gp)
+    (ha, pa), (hb, pb) = grads[fit.FIT_START_CROSSING], grads[fit.FIT_START_LINE]
+    scale = np.maximum(np.abs(ha).reshape(-1, ts.n).max(axis=0), 1e-30)
+    _assert_close(ha, hb, scale, "hit gradients, crossing vs line start")
+    pscale = np.maximum(np.abs(pa).max(axis=0), 1e-30)
+    _assert_close(pa, pb, pscale, "parameter gradients, crossing vs line start")

@@ -155,14 +155,18 @@ def test_f64_finder_with_the_most_candidates():
         f.close()
 
 
-def test_one_candidate_is_the_fit():
+@pytest.mark.parametrize("start", [fit.FIT_START_CROSSING, fit.FIT_START_LINE],
+                         ids=["crossing", "line"])
+def test_one_candidate_is_the_fit(start):
     ts = inputs.generate(inputs.MODE_R, 1000, seed=51)
-    f = fit.Fitter(fit.Geometry(ts.B, ts.surf), None)
+    f = fit.Fitter(fit.Geometry(ts.B, ts.surf, start=start), None)
     try:
         cs = inputs.CandidateSet(ts.hpos[:, None], ts.hcov[:, None], np.zeros((20, ts.n), np.int32))
         got, st = _find(f, ts, cs, np.float32, gate=1e30)
         assert (got["chosen"] == 0).all() and st["tracks"] == ts.n
-        parity.check(got, oracle.fit_set(ts), "finder with one candidate")
+        parity.check(got, oracle.fit_set(ts), f"finder with one candidate, start {start}")
+        per = st["iterations"] / (ts.n * ts.nlayer)
+        assert per < 1.01 if start == fit.FIT_START_CROSSING else per > 1.5
     finally:
         f.close()
 
