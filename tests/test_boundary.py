@@ -80,6 +80,46 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(fit.fit_status) == 48
 
 
+def test_header_compiles_as_c_and_matches_the_binding(tmp_path):
+    """include/fit.h is plain C (C99, -pedantic, no warnings), and a C
+    compiler lays out its structs as the ctypes binding does."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"fit_config": ["B", "nlayer", "surf", "max_iter", "tol", "start"],
+               "fit_launch_config": ["threads_per_block", "blocks_per_sm", "persistent",
+                                     "tracks_per_thread"],
+               "fit_plan_info": ["config", "tracks", "items", "tuned", "best_ms"],
+               "fit_tracks_in": ["par", "cov", "q", "ld"],
+               "fit_tracks_out": ["par", "cov", "q", "chi2", "chi2_layer", "status", "ld"],
+               "fit_hits": ["pos", "cov", "ld"],
+               "fit_status": ["tracks", "no_intersection", "not_converged", "nonfinite",
+                              "charge_flip", "iterations"]}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fit.h"', "int main(void) {"]
+    for name, fields in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for fld in fields:
+            lines.append(f'  printf("{name}.{fld} %zu\\n", offsetof({name}, {fld}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True,
+                                                       text=True, check=True).stdout.split("\n")
+               if line)
+    for name, fields in structs.items():
+        cls = getattr(fit, name)
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fld in fields:
+            assert int(got[f"{name}.{fld}"]) == getattr(cls, fld).offset, f"{name}.{fld}"
+
+
 def test_plan_struct_layouts():
     assert ctypes.sizeof(fit.fit_launch_config) == 16
     assert fit.fit_plan_info.tracks.offset == 16
