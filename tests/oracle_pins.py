@@ -449,6 +449,138 @@ def pin_no_intersection(orc):
     assert st & 1
 
 
+def _flip_case(rng, mode):
+    """A state on the surface whose update drives w = 1/pT through zero: its
+    covariance correlates w strongly with the first measured coordinate and
+    the hit lies on the side that pushes w past zero."""
+    ph, th = rng.uniform(-np.pi, np.pi), rng.uniform(0.5, 2.6)
+    w = 0.02
+    if mode == MODE_R:
+        R = rng.uniform(20, 100)
+        p = np.array([R * np.cos(ph), R * np.sin(ph), rng.uniform(-50, 50), w, ph + 0.05, th])
+        t = np.array([-np.sin(ph), np.cos(ph), 0.0])  # measured direction at the hit
+    else:
+        p = np.array([rng.uniform(-50, 50), rng.uniform(-50, 50), 120.0, w, ph, th])
+        t = np.array([1.0, 0.0, 0.0])
+    sig = np.array([0.1, 0.1, 0.2, 0.1, 0.003, 0.003])
+    corr = np.eye(6)
+    # w correlated (0.9) with the position along t
+    for k in range(3):
+        corr[3, k] = corr[k, 3] = 0.9 * t[k]
+    C = corr * np.outer(sig, sig)
+    if mode == MODE_R:  # no variance along the cylinder normal
+        n = np.array([np.cos(ph), np.sin(ph), 0, 0, 0, 0])
+        P = np.eye(6) - np.outer(n, n)
+        C = P @ C @ P
+    C += np.diag([1e-8, 1e-8, 1e-8, 1e-8, 1e-8, 1e-8])
+    m = p[:3] - 0.25 * t  # the residual along t is -0.25 cm
+    if mode == MODE_R:  # keep the hit on the cylinder
+        m[:2] *= np.hypot(p[0], p[1]) / np.hypot(m[0], m[1])
+    V = 1e-4 * np.outer(t, t) + (1e-2 * np.diag([0, 0, 1.0]) if mode == MODE_R else
+                                 1e-4 * np.diag([0, 1.0, 0]))
+    return p, C, m, V
+
+
+def pin_charge_flip(orc):
+    """An update that drives w through zero.  The oracle's result must be the
+    plain Kalman update (its information form, written here) reparametrised:
+    (w, q) -> (-w, -q), which describes the same helix since kappa = -q kA B w
+    is unchanged, with the covariance transformed by D = diag(1, 1, 1, -1, 1, 1)
+    (row and column 3 negated, C[3][3] kept), and status bit 8 set."""
+    rng = np.random.default_rng(27)
+    D = np.diag([1.0, 1.0, 1.0, -1.0, 1.0, 1.0])
+    for mode in (MODE_R, MODE_Z):
+        for q in (1, -1):
+            for _ in range(4):
+                p, C, m, V = _flip_case(rng, mode)
+                v6 = np.array([V[0, 0], V[1, 0], V[1, 1], V[2, 0], V[2, 1], V[2, 2]])
+                c21 = np.array([C[i, j] for i in range(6) for j in range(i + 1)])
+                st, p1, c1, q1, chi2 = orc.update(mode, q, p, c21, m, v6)
+                # the update without normalisation, in information form
+                Hp, H = _H(mode, m)
+                Vl = Hp @ V @ Hp.T
+                Ci = np.linalg.inv(C)
+                Cp = np.linalg.inv(Ci + H.T @ np.linalg.inv(Vl) @ H)
+                pexp = p + Cp @ H.T @ np.linalg.inv(Vl) @ (Hp @ (m - p[:3]))
+                pexp[4] = _wrap(pexp[4])
+                assert pexp[3] < -0.05, pexp[3]  # the case really crosses zero
+                # (iii) charge negated, status bit set
+                assert q1 == -q and (st & 8), (q1, st)
+                # w flipped, the other parameters as the plain update
+                flip = D @ pexp
+                assert np.allclose(p1, flip, rtol=1e-9, atol=1e-11), (p1, flip)
+                assert p1[3] > 0
+                # (ii) C' = D Cp D, including an unchanged C[3][3]
+                C1 = _sym6(c1)
+                d = np.sqrt(np.outer(np.diag(Cp), np.diag(Cp)))
+                assert np.abs((C1 - D @ Cp @ D) / d).max() < 1e-8
+                assert C1[3, 3] > 0 and abs(C1[3, 3] - Cp[3, 3]) < 1e-9 * Cp[3, 3]
+                # (i) the flipped state (w > 0, -q) and the plain one (w < 0, q)
+                # are the same helix
+                for h in (0.5, 7.0, 40.0):
+                    a, b = orc.helix(B, q1, p1, h), orc.helix(B, q, pexp, h)
+                    assert np.allclose(a[:3], b[:3], rtol=0, atol=1e-9), (h, a, b)
+                    assert abs(_wrap(a[4] - b[4])) < 1e-12
+                # and reach a surface at the same point
+                s_next = (np.hypot(p1[0], p1[1]) + 10.0) if mode == MODE_R else p1[2] + 20.0
+                if mode == MODE_Z and np.cos(p1[5]) < 0:
+                    s_next = p1[2] - 20.0
+                sa, pa, _, ha = orc.transport(mode, B, s_next, q1, p1)
+                sb, pb, _, hb = orc.transport(mode, B, s_next, q, pexp)
+                assert sa == sb
+                if sa == 0:
+                    assert abs(ha - hb) < 1e-9 * max(1.0, ha)
+                    assert np.allclose(pa[:3], pb[:3], rtol=0, atol=1e-9)
+    # and no flip while w stays positive
+    p, C, m, V = _flip_case(rng, MODE_Z)
+    m = p[:3] + 0.25 * np.array([1.0, 0.0, 0.0])
+    v6 = np.array([V[0, 0], V[1, 0], V[1, 1], V[2, 0], V[2, 1], V[2, 2]])
+    c21 = np.array([C[i, j] for i in range(6) for j in range(i + 1)])
+    st, p1, _, q1, _ = orc.update(MODE_Z, 1, p, c21, m, v6)
+    assert q1 == 1 and not (st & 8) and p1[3] > p[3]
+
+
+def _reverse(p):
+    """The same point with the momentum reversed: phi + pi, pi - theta (the
+    charge is negated beside it).  kappa changes sign, so the reversed track
+    runs back along the same curve."""
+    r = p.copy()
+    r[4] = _wrap(p[4] + np.pi)
+    r[5] = np.pi - p[5]
+    return r
+
+
+def pin_reversibility(orc):
+    """Propagating to a surface and then, with the momentum reversed, back to
+    the start surface returns the start state (to ~1e-12), and the composed
+    surface-to-surface Jacobians are the identity on the start surface's
+    tangent space."""
+    rng = np.random.default_rng(28)
+    Dr = np.diag([1.0, 1.0, 1.0, 1.0, 1.0, -1.0])  # d(reverse)/dp
+    for mode in (MODE_R, MODE_Z):
+        for p, q, s1 in _states(rng, 15, mode):
+            if mode == MODE_R:
+                s0 = float(np.hypot(p[0], p[1]))
+                if s0 < 1.0:
+                    continue
+                tang = [np.array([-p[1], p[0], 0, 0, 0, 0]) / s0] + [np.eye(6)[k] for k in (2, 3, 4, 5)]
+            else:
+                s0 = float(p[2])
+                tang = [np.eye(6)[k] for k in (0, 1, 3, 4, 5)]
+            st, p1, J1, h1 = orc.transport(mode, B, s1, q, p)
+            assert st == 0
+            st, p2, J2, h2 = orc.transport(mode, B, s0, -q, _reverse(p1))
+            assert st == 0
+            back = _reverse(p2)
+            d = back - p
+            d[4] = _wrap(d[4])
+            assert np.all(np.abs(d) <= 1e-12 * np.maximum(np.abs(p), 1.0)), (p, back)
+            assert abs(h1 - h2) <= 1e-10 * max(1.0, h1)
+            Jt = Dr @ J2 @ Dr @ J1
+            for v in tang:
+                assert np.allclose(Jt @ v, v, rtol=0, atol=1e-10 * max(1.0, np.abs(J1).max())), (mode, v, Jt @ v)
+
+
 def _covs_pd_on_surface(mode, par, cov, surf_last):
     for i in range(par.shape[1]):
         C = _sym6(cov[:, i])
@@ -603,6 +735,8 @@ ALL_PINS = [
     pin_update_limits,
     pin_update_information_form,
     pin_propagated_covariance,
+    pin_charge_flip,
+    pin_reversibility,
     pin_no_intersection,
     pin_filter_consistency,
     pin_chi2_gradient_fd,

@@ -38,6 +38,13 @@ MUTANTS = {
     "find_tries_candidates_on_the_track": (
         "T c = kalman_update(mode, trial, cpos[l * ncand + k], ccov[l * ncand + k], ignored);",
         "T c = kalman_update(mode, t, cpos[l * ncand + k], ccov[l * ncand + k], ignored);"),
+    "flip_keeps_the_charge": ("    t.q = -t.q;\n", "\n"),
+    "flip_keeps_the_sign_of_w": ("    t.p[PW] = -t.p[PW];\n", "\n"),
+    "flip_negates_the_w_variance": ("    st |= ST_CHARGE_FLIP;",
+                                    "    t.C[PW][PW] = -t.C[PW][PW];\n    st |= ST_CHARGE_FLIP;"),
+    "flip_leaves_the_covariance": ("      t.C[PW][i] = -t.C[PW][i];\n      t.C[i][PW] = -t.C[i][PW];\n", ""),
+    "helix_z_uses_tan": ("out[PZ] = p[PZ] + h * cos(p[PTHETA]) / sin(p[PTHETA]);",
+                         "out[PZ] = p[PZ] + h * sin(p[PTHETA]) / cos(p[PTHETA]);"),
 }
 
 
