@@ -33,29 +33,35 @@ NEVT, NTRK, NLAYER, SEED = 100, 9600, 20, 2
 # The headline metric: track-layers per second (the value), reported with the
 # roofline fraction and the CPU oracle beside it.
 METRIC = "track-layer propagate+update/s on 1 GB300; % of FP32/HBM roofline vs oracle"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
+MUFU_LANES_PER_SM = 16
 
-# Algorithmic work per track-layer: FP32 flops of the kernel's formulas (FMA
-# = 2), as executed with one track per thread and counted by ncu (FFMA x 2 +
-# FADD + FMUL thread instructions, 20-event workload; p2r from the closed-form
-# crossing start, one path-length iteration per track-layer;
-# profiles/fit_fused_*_100x9600x20.md), and bytes (hit 36 B + track state in
-# and out 229 B / nlayer).
-FLOPS_P2Z = 489.0
-FLOPS_P2R = 700.0
-# p2r from the straight-line start: 723 flops at its measured 2.007 iterations
-# per track-layer.  With the crossing start's ~22 more flops (its closed form
-# against the straight-line distance) the two counts give ~45 flops per
-# path-length iteration; a kernel that starts on the straight line and takes
-# `it` iterations is counted as FLOPS_P2R_LINE - 45 (2.007 - it).
-FLOPS_P2R_LINE = 723.0
-FLOPS_P2R_ITERATION = 45.0
+# Algorithmic work per track-layer: a fixed count of the FP32 operations of
+# the method's formulas (FMA = 2), the same for every build of the kernel, so
+# that a leaner kernel raises the roofline fraction instead of lowering it.
+#   p2z: helix to the plane ~30, Jacobian and J C J^T (sparse) ~330, 2-D
+#        Kalman update (gain, state, covariance, chi2) ~220: 580.
+#   p2r: ~600 outside the path-length iteration, ~50 per iteration (helix at
+#        h and the straight-line step to the cylinder); the iterations per
+#        track-layer are counted by the kernel on every run.
+# MUFU (sin/cos, square root, reciprocal) operations per track-layer: p2z 3
+# sin/cos + 1 reciprocal; p2r 1 sin/cos + 1 atan2 or rsqrt + per iteration 1
+# sin/cos + 1 square root.
+FLOPS_P2Z = 580.0
+FLOPS_P2R_FIXED = 600.0
+FLOPS_P2R_PER_ITERATION = 50.0
+MUFU_P2Z = 4.0
 
 
-def flops_p2r_line(iterations: float) -> float:
-    return FLOPS_P2R_LINE - FLOPS_P2R_ITERATION * (2.007 - iterations)
+def flops_p2r(iterations: float) -> float:
+    return FLOPS_P2R_FIXED + FLOPS_P2R_PER_ITERATION * iterations
+
+
+def mufu_p2r(iterations: float) -> float:
+    return 2.0 + 2.0 * iterations
+
+
 BYTES_TRACK_IN = (6 + 21 + 1) * 4
 BYTES_TRACK_OUT = (6 + 21 + 1 + 1) * 4 + 1
 
@@ -79,19 +85,65 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": SM_MAX_MHZ_NOMINAL}
 
 
-def fp32_peak_tflops(mhz: float) -> float:
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+def fp32_peak_tflops(mhz: float, sms: int) -> float:
+    """FP32 ceiling from unit counts: SMs x 128 FP32 lanes x 2 flops x clock."""
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def mufu_peak_tops(mhz: float, sms: int) -> float:
+    return sms * MUFU_LANES_PER_SM * mhz * 1e6 / 1e12
+
+
+def sm_count(local: int) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(local).multi_processor_count)
+
+
+def measure_fp32(local: int) -> dict:
+    """The FP32 throughput probe (fit_probe_fp32) on this device, scalar and
+    packed FMAs, with the SM clock sampled while it runs: checks the derived
+    FP32 ceiling against the hardware."""
+    import torch
+    from paper_2409_09228_gb300 import fit
+    dev = torch.device("cuda", local)
+    sms = sm_count(local)
+    blocks = sms * 8 * 4  # 8 resident blocks of 256 per SM, 4 waves
+    out = torch.empty(blocks * fit.FIT_PROBE_THREADS, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    for packed, name in ((0, "ffma"), (1, "ffma2")):
+        iters = 2048 if packed else 4096
+        for _ in range(2):
+            fit.fit_probe_fp32(packed, blocks, iters, out, stream)
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flops = fit.fit_probe_fp32(packed, blocks, iters, out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            best = min(best, e0.elapsed_time(e1))
+        res[f"{name}_tflops"] = flops / (best / 1e3) / 1e12
+    clk = clocks.stop()
+    res["sm_mhz"] = clk["sm_mhz"]
+    res["sms"] = sms
+    if clk["sm_mhz"]:
+        res["derived_at_this_clock_tflops"] = fp32_peak_tflops(clk["sm_mhz"], sms)
+    return res
 
 
 # The sources fit_fused_kernel is compiled from (and the constants it takes
-# from include/fit.h); the DRAM traffic committed under profiles/ holds only
-# while their code (comments and layout aside) hashes to the value recorded
-# there.
+# from include/fit.h): a DRAM traffic figure measured by ncu holds only while
+# their code (comments and layout aside) hashes to the value stored with it.
 FUSED_SOURCES = ("paper_2409_09228_gb300/csrc/fit.cu",
                  "paper_2409_09228_gb300/csrc/fused.cuh",
                  "paper_2409_09228_gb300/csrc/track_math.cuh",
                  "paper_2409_09228_gb300/csrc/lanes.cuh",
                  "paper_2409_09228_gb300/csrc/internal.h")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
 
 def code_only(text: str) -> str:
@@ -130,16 +182,16 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic(kernel: str) -> float | None:
-    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{NEVT}x{NTRK}x{NLAYER}.md")
-    if not os.path.exists(path):
+    """DRAM bytes (read + write) per launch of `kernel` on this workload, as
+    ncu measured them, if they were measured on the current source."""
+    if not os.path.exists(TRAFFIC_FILE):
         return None
-    text = open(path).read()
-    m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
-    m_val = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_val or m_hash.group(1) != kernel_source_hash():
+    with open(TRAFFIC_FILE) as f:
+        entries = json.load(f)
+    e = entries.get(f"{kernel}_{NEVT}x{NTRK}x{NLAYER}")
+    if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return float(m_val.group(1))
+    return float(e["dram_bytes_per_launch"])
 
 
 class ClockSampler:
@@ -485,7 +537,8 @@ def bench_f64(args, world, rank, local):
         return
     tl = n * NLAYER
     kms = [statistics.mean(k) for k in kern]
-    ach = FLOPS_P2R * tl / (kms[0] / 1e3) / 1e12
+    it_f64 = st["iterations"] / (args.steps * tl)
+    ach = flops_p2r(it_f64) * tl / (kms[0] / 1e3) / 1e12
     line = {"metric": "track-layer propagate+update/s", "value": world * 2 * tl / (ms / 1e3),
             "unit": "track-layer/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -498,7 +551,7 @@ def bench_f64(args, world, rank, local):
                          "unit": "TFLOP/s (FP64)", "frac": ach / FP64_PEAK_TFLOPS_NOMINAL,
                          "peak_source": "nominal GB300 FP64 rate", "traffic": None,
                          "kernel": "fit_f64_kernel<p2r>", "kernel_ms_p2r_p2z": kms,
-                         "flops_per_track_layer": FLOPS_P2R},
+                         "flops_per_track_layer": flops_p2r(it_f64)},
             "clocks": clk, "gpu_launches": 2 * args.steps,
             "p2r_iterations_per_track_layer": st["iterations"] / (args.steps * tl)}
     print(json.dumps(line))
@@ -758,8 +811,8 @@ def bench_seed(args, world, rank, local):
     ms = res["network"]["ms"]
     tl = n * NLAYER
     peaks = load_peaks()
-    alu_peak = fp32_peak_tflops(peaks["sm_max_mhz"])
-    seeded_flops = flops_p2r_line(res["network"]["iterations_per_track_layer"])
+    alu_peak = fp32_peak_tflops(peaks["sm_max_mhz"], sm_count(local))
+    seeded_flops = flops_p2r(res["network"]["iterations_per_track_layer"])
     alu_ach = seeded_flops * tl / (ms / 1e3) / 1e12
     mlp_flops = 2.0 * 4801  # multiply-adds of the network per track-layer, x 2
     line = {"metric": "track-layer propagate+update/s", "value": res["network"]["value"],
@@ -864,6 +917,7 @@ def main():
             if events is not None:
                 events[m][1].record(stream)
 
+    fp32_probe = measure_fp32(local)
     for _ in range(args.warmup):
         step()
     st = f.sync(stream)
@@ -891,31 +945,41 @@ def main():
     units_per_step = 2 * n * NLAYER
     value = world * units_per_step / (ms / 1e3)
 
-    # iterations of the p2r path-length step (the flop count assumes 1.0)
-    it_per = st.get("iterations", 0) / max(1, args.steps * n * NLAYER) if "iterations" in st else None
-    flops = [FLOPS_P2R, FLOPS_P2Z]
+    # iterations of the p2r path-length step per track-layer, counted by the kernel
+    it_per = st["iterations"] / max(1, args.steps * n * NLAYER)
+    flops = [flops_p2r(it_per), FLOPS_P2Z]
+    mufu = [mufu_p2r(it_per), MUFU_P2Z]
     dom = int(np.argmax(kernel_ms))
     name = ["fit_fused_p2r", "fit_fused_p2z"][dom]
     peaks = load_peaks()
-    alu_peak = fp32_peak_tflops(peaks["sm_max_mhz"])
+    sms = sm_count(local)
+    alu_peak = fp32_peak_tflops(peaks["sm_max_mhz"], sms)
     tl = n * NLAYER
+    bpl = bytes_per_track_layer(NLAYER)
     alu_ach = flops[dom] * tl / (kernel_ms[dom] / 1e3) / 1e12
-    hbm_ach = bytes_per_track_layer(NLAYER) * tl / (kernel_ms[dom] / 1e3) / 1e9
+    hbm_ach = bpl * tl / (kernel_ms[dom] / 1e3) / 1e9
     t_alu = flops[dom] * tl / (alu_peak * 1e12)
-    t_hbm = bytes_per_track_layer(NLAYER) * tl / (peaks["hbm_gbs"] * 1e9)
+    t_hbm = bpl * tl / (peaks["hbm_gbs"] * 1e9)
+    t_mufu = mufu[dom] * tl / (mufu_peak_tops(peaks["sm_max_mhz"], sms) * 1e12)
     traffic = profiled_traffic(name)
     if t_alu >= t_hbm:
         roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": alu_ach / alu_peak,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz"}
+                "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                               f"{peaks['sm_max_mhz']:.0f} MHz (max SM clock, "
+                               f"{'MEASURED_PEAKS.json' if peaks['source'] == 'measured' else 'nominal'})"}
     else:
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm_ach / peaks["hbm_gbs"], "peak_source": peaks["source"]}
     roof.update({"traffic": traffic, "kernel": name, "kernel_ms": kernel_ms[dom],
-                 "flops_per_track_layer": flops[dom],
-                 "bytes_per_track_layer": bytes_per_track_layer(NLAYER),
+                 "flops_per_track_layer": flops[dom], "mufu_per_track_layer": mufu[dom],
+                 "bytes_per_track_layer": bpl,
                  "hbm_frac": hbm_ach / peaks["hbm_gbs"], "alu_frac": alu_ach / alu_peak,
-                 "kernel_ms_p2r_p2z": kernel_ms})
+                 "t_roof_us": {"alu": t_alu * 1e6, "hbm": t_hbm * 1e6, "mufu": t_mufu * 1e6},
+                 "kernel_ms_p2r_p2z": kernel_ms,
+                 "frac_p2r_p2z": [max(flops[m] * tl / (alu_peak * 1e12), t_hbm) /
+                                  (kernel_ms[m] / 1e3) for m in (0, 1)],
+                 "fp32_probe": fp32_probe})
 
     # End to end through the C ABI on host buffers: one fit_propagate_update_host
     # call per step copies both modes' tracks and hits (the p2r events, then the

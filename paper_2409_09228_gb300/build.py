@@ -1,8 +1,9 @@
 """Builds libfit.so in place with nvcc for sm_103a (GB300).
 
 Used by ``__graft_entry__.build()`` and on first import of the binding when the
-library is missing or older than its sources.  One translation unit, one
-``-gencode``: a few seconds on any host with nvcc, no GPU needed.
+library is missing or older than its sources.  Every translation unit is
+compiled to an object in parallel (one ``-gencode``), then linked: no GPU
+needed.
 """
 from __future__ import annotations
 
@@ -34,9 +35,52 @@ def nvcc() -> str:
     return "nvcc"
 
 
+FLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-v", "-Xcompiler", "-fPIC"]
+
+
 def command(out: str = LIB) -> list:
-    return [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-v", "-I" + INCLUDE,
-            "-Xcompiler", "-fPIC", "-shared", *sources(), "-o", out]
+    """One nvcc command for the whole library (serial over the sources)."""
+    return [nvcc(), *FLAGS, "-I" + INCLUDE, "-shared", *sources(), "-o", out]
+
+
+def compile_commands(objdir: str) -> list:
+    """(source, object, command) for every translation unit."""
+    out = []
+    for src in sources():
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        out.append((src, obj, [nvcc(), *FLAGS, "-I" + INCLUDE, "-c", src, "-o", obj]))
+    return out
+
+
+def link_command(objs: list, out: str) -> list:
+    return [nvcc(), ARCH, "-shared", *objs, "-o", out]
+
+
+def build_objects(out: str, verbose: bool = False) -> None:
+    """Compiles the sources in parallel and links them into `out`."""
+    import shutil
+    import tempfile
+    objdir = tempfile.mkdtemp(prefix="libfit_obj_")
+    try:
+        jobs = [(src, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT,
+                                            text=True))
+                for src, obj, cmd in compile_commands(objdir)]
+        failed, logs = [], []
+        for src, obj, proc in jobs:
+            text, _ = proc.communicate()
+            logs.append(text)
+            if proc.returncode != 0:
+                failed.append(f"{os.path.basename(src)}:\n{text}")
+        if failed:
+            raise RuntimeError("nvcc failed building libfit.so:\n" + "\n".join(failed))
+        r = subprocess.run(link_command([o for _, o, _ in jobs], out), capture_output=True,
+                           text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed linking libfit.so:\n" + r.stdout + r.stderr)
+        if verbose:
+            print("".join(logs))
+    finally:
+        shutil.rmtree(objdir, ignore_errors=True)
 
 
 def up_to_date() -> bool:
@@ -50,11 +94,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run(command(tmp), capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc failed building libfit.so:\n" + r.stdout + r.stderr)
-    if verbose:
-        print(r.stderr)
+    build_objects(tmp, verbose)
     os.replace(tmp, LIB)
     return LIB
 

@@ -201,7 +201,7 @@ struct fit_plan {
   unsigned* d_work = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
-  const void* key_ptrs[11] = {};
+  const void* key_ptrs[12] = {};
   unsigned long long* d_tune_counters = nullptr;  // counters of the tuning runs
   int64_t key_ld[3] = {};
   int tuned = 0;
@@ -311,8 +311,9 @@ void drop_graph(fit_plan* p) {
 // set and shape) and launches it on s.
 int run_graph(fit_plan* p, const fit_tracks_in* in, const fit_tracks_out* out,
               const fit_hits* hits, cudaStream_t s, unsigned long long* counters) {
-  const void* ptrs[11] = {in->par, in->cov, in->q, out->par, out->cov, out->q,
-                          out->chi2, out->chi2_layer, out->status, hits->pos, counters};
+  const void* ptrs[12] = {in->par, in->cov, in->q, out->par, out->cov, out->q,
+                          out->chi2, out->chi2_layer, out->status, hits->pos, hits->cov,
+                          counters};
   const int64_t lds[3] = {in->ld, out->ld, hits->ld};
   const bool same = p->exec && std::memcmp(ptrs, p->key_ptrs, sizeof(ptrs)) == 0 &&
                     std::memcmp(lds, p->key_ld, sizeof(lds)) == 0;

@@ -209,6 +209,9 @@ def load(build_if_missing: bool = True):
     L.fit_mlp_attach.restype = ctypes.c_int
     L.fit_path_lengths.argtypes = [vp, vp, i64, vp, vp, i64, vp, i32p, ctypes.c_int, vp]
     L.fit_path_lengths.restype = ctypes.c_int
+    L.fit_probe_fp32.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                 ctypes.POINTER(ctypes.c_double)]
+    L.fit_probe_fp32.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -647,6 +650,22 @@ def fit_destroy(h: int) -> None:
 
 def fit_last_error() -> str:
     return load().fit_last_error().decode()
+
+
+FIT_PROBE_THREADS = 256
+
+
+def fit_probe_fp32(packed: bool, blocks: int, iters: int, out, stream=None) -> float:
+    """Queues the FP32 throughput probe (include/fit_probe.h) on `stream`;
+    `out` holds at least blocks x FIT_PROBE_THREADS floats.  Returns the
+    launch's FP32 flops (FMA = 2)."""
+    if out.numel() < blocks * FIT_PROBE_THREADS:
+        raise FitError(FIT_ERR_ARG, "fit_probe_fp32: out is too small")
+    flops = ctypes.c_double()
+    _check(load().fit_probe_fp32(int(bool(packed)), int(blocks), int(iters),
+                                 ctypes.c_void_p(out.data_ptr()), _stream_handle(stream),
+                                 ctypes.byref(flops)))
+    return float(flops.value)
 
 
 class Fitter:

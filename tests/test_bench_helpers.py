@@ -1,6 +1,6 @@
 """bench.py's host-side helpers (no GPU): the code-only source hash that
-decides whether the committed ncu traffic still applies, and the flop count
-of the straight-line start."""
+decides whether the committed ncu traffic still applies, and the fixed
+algorithmic flop count."""
 import os
 import sys
 
@@ -19,6 +19,10 @@ def test_code_only_drops_comments_and_layout_but_keeps_literals():
     assert bench.code_only(a) != bench.code_only(a.replace("2 * x", "3 * x"))
 
 
-def test_flop_count_of_the_straight_line_start():
-    assert bench.flops_p2r_line(2.007) == bench.FLOPS_P2R_LINE
-    assert bench.flops_p2r_line(1.0) < bench.FLOPS_P2R_LINE
+def test_fixed_flop_count():
+    """The algorithmic count depends on the iterations a run takes, never on
+    the build: p2r 600 + 50 per iteration, p2z 580."""
+    assert bench.flops_p2r(1.0) == 650.0
+    assert bench.flops_p2r(2.0) == 700.0
+    assert bench.FLOPS_P2Z == 580.0
+    assert bench.fp32_peak_tflops(2070.0, 152) == 152 * 128 * 2 * 2070e6 / 1e12

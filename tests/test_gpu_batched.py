@@ -1,6 +1,7 @@
 """The batched persistent form (fit_plan_*): uneven events of both modes in one
 launch under a CUDA graph, against the FP64 oracle and against the per-segment
 path; every launch shape the autotuner can pick; the tuning cache."""
+import dataclasses
 import os
 
 import numpy as np
@@ -89,6 +90,41 @@ def test_plan_matches_oracle_and_segments():
         fit.fit_plan_destroy(plan)
         f.close()
 
+
+
+def test_plan_recaptures_for_a_new_hit_covariance_buffer():
+    """Two runs with the same hit-position buffer and a different
+    hit-covariance buffer: the second must read the new covariances (the
+    captured graph is keyed on every buffer it reads), not replay the first
+    run's pointer."""
+    ev = _events(30, seed=37)
+    ld, dev_in = _device(ev)
+    f = fit.Fitter(*_geoms(ev))
+    plan = fit.fit_plan_create(f.h, ev.ntrk, ev.mode, 20)
+    try:
+        hcov2 = dev_in[4] * 4.0  # every hit error doubled
+        ev2 = dataclasses.replace(ev, hcov=ev.hcov * np.float32(4.0))
+        runs = []
+        for hc in (dev_in[4], hcov2):
+            out = _outputs(f, ev, ld)
+            fit.fit_plan_run(plan, dev_in[0], dev_in[1], dev_in[2], dev_in[3], hc,
+                             par_out=out["par"], cov_out=out["cov"], q_out=out["q"],
+                             chi2=out["chi2"], status=out["status"])
+            f.sync()
+            runs.append(_fetch(out, ev.n))
+        # the segment path with the same buffers is the reference for each run
+        for hc, got, label in ((dev_in[4], runs[0], "first hcov"), (hcov2, runs[1], "second hcov")):
+            ref = _fetch(f.run(dev_in[0], dev_in[1], dev_in[2], dev_in[3], hc, ev.ntrk, ev.mode),
+                         ev.n)
+            f.sync()
+            parity.check(got, ref, f"plan, {label}")
+        ok = (runs[0]["status"] == 0) & (runs[1]["status"] == 0)
+        # larger hit errors, smaller chi2: the second run did read the new buffer
+        assert runs[1]["chi2"][ok].mean() < 0.5 * runs[0]["chi2"][ok].mean()
+        _check_against_oracle(ev2, runs[1], "plan, second hcov")
+    finally:
+        fit.fit_plan_destroy(plan)
+        f.close()
 
 @pytest.mark.parametrize("tpb,bps,persistent,tpt", [(64, 1, 1, 2), (64, 6, 1, 2), (128, 1, 1, 2),
                                                     (128, 3, 1, 2), (32, 12, 1, 2), (32, 1, 1, 2),
