@@ -181,13 +181,21 @@ int fit_sync(fit_handle* h, void* stream, double timeout_s, fit_status* st);
  *   per_event     HOST array of nevt fit_status, or NULL.  If given, the call
  *                 waits for its work on `stream` and fills entry e with the
  *                 counts of event e (tracks = ntrk[e]).  If NULL the call
- *                 returns as soon as its work is queued.
+ *                 does not wait for its kernels; but the event offsets are
+ *                 copied to the device from a local (pageable) host array,
+ *                 and for such a copy the CUDA driver may wait for the work
+ *                 queued earlier on `stream` before the call returns.
  * The work runs on the current CUDA device.  The first call on a device looks
  * up the device address of the fixed array (once per device); make that first
- * call before any stream capture begins.  Every call shares the one array and
- * each call clears the counters of its own events before its kernels run, so
- * calls whose work overlaps on the GPU (other streams, other host threads)
- * race on it: serialise them.
+ * call before any stream capture begins.  That first call may also be where
+ * CUDA loads the library's kernels onto the device (with lazy module loading,
+ * CUDA's default), which allocates device memory for their code and for the
+ * fixed array: make the first call while the process may still allocate (at
+ * start-up), or set CUDA_MODULE_LOADING=EAGER so that loading happens when the
+ * library is loaded.  Later calls allocate nothing.  Every call shares the one
+ * array and each call clears the counters of its own events before its
+ * kernels run, so calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on it: serialise them.
  */
 #define FIT_NOALLOC_MAX_EVENTS 4096
 

@@ -262,6 +262,123 @@ __device__ __forceinline__ void similarity(const T (&E)[6][6], T (&c)[21]) {
     }
 }
 
+// c <- J c J^T through the structure of the propagate-to-surface Jacobian,
+// J = A + v g^T: A = I + E_h is the derivative of the helix at a fixed path
+// length h, v = d p' / d h, and g = grad h, the dependence of h on the
+// input state (the surface constraint).  With m = c g and s = g^T m,
+//   J c J^T = A c A^T + n v^T + v n^T,   n = A m + (s / 2) v,
+// so the dense product is replaced by a sparse similarity with A and a
+// symmetric rank-2 update.  A's off-diagonal entries are those of E_h:
+// row x: f03 (d x'/d w), f04 (d x'/d phi); row y: f13, f14; row z: f25
+// (d z'/d theta, p2r only); row phi: g43 (d phi'/d w).  A factors as
+// (I + G)(I + F), F holding rows x, y, z (which read only rows w, phi, theta,
+// unchanged by F) and G the phi row, so both steps run in place.  VZ = false
+// (p2z): the z row of J vanishes (z' = Z on the plane), so row and column z
+// of the result are zero and v, g carry no z component in the result; GMASK
+// and VMASK mark the components of g and v that can be non-zero.
+template <bool P2R, unsigned GMASK, unsigned VMASK, class T>
+__device__ __forceinline__ void similarity_rank1(T (&c)[21], T f03, T f04, T f13, T f14, T f25,
+                                                 T g43, const T (&gr)[6], const T (&v)[6]) {
+  // m = c g (with the input covariance), s = g^T m
+  T m[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    T acc = T(0.f);
+    bool first = true;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (GMASK & (1u << k)) {
+        acc = first ? c[sym(i, k)] * gr[k] : fma(c[sym(i, k)], gr[k], acc);
+        first = false;
+      }
+    m[i] = acc;
+  }
+  T sg = T(0.f);
+  {
+    bool first = true;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (GMASK & (1u << k)) {
+        sg = first ? gr[k] * m[k] : fma(gr[k], m[k], sg);
+        first = false;
+      }
+  }
+  // F step: rows x, y (and z) from rows w, phi, theta.  Row i of F c F^T
+  // (j <= i) needs the input cross block of rows j <= i and row i's new
+  // cross block X_il = c_il + sum_k F_ik c_kl, so the rows run from the last
+  // to the first and each overwrites its own cross block when it is done.
+  constexpr int NF = P2R ? 3 : 2;
+  const T F[3][3] = {{f03, f04, T(0.f)}, {f13, f14, T(0.f)}, {T(0.f), T(0.f), f25}};
+  auto Fik = [&](int i, int k) -> T { return F[i][k - 3]; };
+  auto Fnz = [](int i, int k) -> bool { return (i < 2 && k < 5) || (i == 2 && k == 5); };
+#pragma unroll
+  for (int i = NF - 1; i >= 0; --i) {
+    T X[3];
+#pragma unroll
+    for (int l = 3; l < 6; ++l) {
+      T acc = c[sym(i, l)];
+#pragma unroll
+      for (int k = 3; k < 6; ++k)
+        if (Fnz(i, k)) acc = fma(Fik(i, k), c[sym(k, l)], acc);
+      X[l - 3] = acc;
+    }
+    // c_ij <- c_ij + sum_k F_ik c_kj + sum_l X_il F_jl
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      T acc = c[sym(i, j)];
+#pragma unroll
+      for (int k = 3; k < 6; ++k)
+        if (Fnz(i, k)) acc = fma(Fik(i, k), c[sym(k, j)], acc);
+#pragma unroll
+      for (int l = 3; l < 6; ++l)
+        if (Fnz(j, l)) acc = fma(X[l - 3], Fik(j, l), acc);
+      c[sym(i, j)] = acc;
+    }
+#pragma unroll
+    for (int l = 3; l < 6; ++l) c[sym(i, l)] = X[l - 3];
+  }
+  if constexpr (!P2R) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) c[sym(2, j)] = T(0.f);
+  }
+  // G step: row phi += g43 row w (and column phi likewise)
+  {
+    const T c43 = c[sym(4, 3)];
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      if (j != 3 && j != 4 && (P2R || j != 2)) c[sym(4, j)] = fma(g43, c[sym(3, j)], c[sym(4, j)]);
+    const T c43n = fma(g43, c[sym(3, 3)], c43);
+    c[sym(4, 3)] = c43n;
+    c[sym(4, 4)] = fma(g43, c43 + c43n, c[sym(4, 4)]);
+  }
+  // n = A m + (s / 2) v, A = (I + G)(I + F)
+  T n[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) n[i] = m[i];
+#pragma unroll
+  for (int i = 0; i < NF; ++i)
+#pragma unroll
+    for (int k = 3; k < 6; ++k)
+      if (Fnz(i, k)) n[i] = fma(Fik(i, k), m[k], n[i]);
+  if constexpr (!P2R) n[2] = T(0.f);
+  n[4] = fma(g43, n[3], n[4]);
+  const T hs = T(0.5f) * sg;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    if (VMASK & (1u << i)) n[i] = fma(hs, v[i], n[i]);
+  // c += n v^T + v n^T
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      if (!P2R && (i == 2 || j == 2)) continue;
+      T acc = c[sym(i, j)];
+      if (VMASK & (1u << j)) acc = fma(n[i], v[j], acc);
+      if (VMASK & (1u << i)) acc = fma(v[i], n[j], acc);
+      c[sym(i, j)] = acc;
+    }
+}
+
 // Propagation to the plane z = Z.  Returns the mask of lanes whose plane is
 // behind them; if any lane fails nothing is modified.
 template <class T>
@@ -286,19 +403,12 @@ __device__ __forceinline__ typename Lanes<T>::M prop_z(T (&p)[6], T (&c)[21], Tr
   turn(c1, s1, cu, su);  // phi + 2u = phi'
   const T hh = T(0.5f) * h * h * dkdw;
   const T hth = fdiv(dz, g.cth * g.cth);  // dh/dtheta
-  T E[6][6];
-  E[0][2] = -(c1 * tanth);
-  E[0][3] = hh * fma(sp, cm, -(s * sm));
-  E[0][4] = -dy;
-  E[0][5] = c1 * hth;
-  E[1][2] = -(s1 * tanth);
-  E[1][3] = hh * fma(sp, sm, s * cm);
-  E[1][4] = dx;
-  E[1][5] = s1 * hth;
-  E[4][2] = -(kappa * tanth);
-  E[4][3] = h * dkdw;
-  E[4][5] = kappa * hth;
-  similarity<kRowsZ, kEZ>(E, c);
+  // grad h = (0, 0, -tan(theta), 0, 0, dh/dtheta); d p'/d h = (cos phi',
+  // sin phi', 0 on the plane, 0, kappa, 0)
+  const T gr[6] = {T(0.f), T(0.f), -tanth, T(0.f), T(0.f), hth};
+  const T v[6] = {c1, s1, T(0.f), T(0.f), kappa, T(0.f)};
+  similarity_rank1<false, (1u << 2) | (1u << 5), (1u << 0) | (1u << 1) | (1u << 4)>(
+      c, hh * fma(sp, cm, -(s * sm)), -dy, hh * fma(sp, sm, s * cm), dx, T(0.f), h * dkdw, gr, v);
   p[0] += dx;
   p[1] += dy;
   p[2] = T(Z);
@@ -552,25 +662,12 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
   const T hx = -(px * iD), hy = -(py * iD);
   const T hw = -(fma(px, Xw, py * Yw) * iD);
   const T hp = fma(px, dy, -(py * dx)) * iD;
-  T E[6][6];
-  E[0][0] = c1 * hx;
-  E[0][1] = c1 * hy;
-  E[0][3] = fma(c1, hw, Xw);
-  E[0][4] = fma(c1, hp, -dy);
-  E[1][0] = s1 * hx;
-  E[1][1] = s1 * hy;
-  E[1][3] = fma(s1, hw, Yw);
-  E[1][4] = fma(s1, hp, dx);
-  E[2][0] = cot * hx;
-  E[2][1] = cot * hy;
-  E[2][3] = cot * hw;
-  E[2][4] = cot * hp;
-  E[2][5] = -(h * isth * isth);
-  E[4][0] = kappa * hx;
-  E[4][1] = kappa * hy;
-  E[4][3] = fma(kappa, hw, h * dkdw);
-  E[4][4] = kappa * hp;
-  similarity<kRowsR, kER>(E, c);
+  // d p'/d h = (cos phi', sin phi', cot theta, 0, kappa, 0)
+  const T gr[6] = {hx, hy, T(0.f), hw, hp, T(0.f)};
+  const T v[6] = {c1, s1, cot, T(0.f), kappa, T(0.f)};
+  similarity_rank1<true, (1u << 0) | (1u << 1) | (1u << 3) | (1u << 4),
+                   (1u << 0) | (1u << 1) | (1u << 2) | (1u << 4)>(
+      c, Xw, -dy, Yw, dx, -(h * isth * isth), h * dkdw, gr, v);
   p[0] = px;
   p[1] = py;
   p[2] = fma(h, cot, p[2]);
@@ -583,46 +680,70 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
 
 // Kalman update with a 2-D measurement: a and b are the columns of C H^T (the
 // two measured directions), S = H C H^T + H V H^T, K = C H^T S^-1,
-// p += K r, C -= K (H C), chi2 = r^T S^-1 r.
+// p += K r, C -= K S K^T, chi2 = r^T S^-1 r.  Evaluated in square-root form:
+// with the Cholesky factor S = L L^T, U = [a b] L^-T and z = L^-1 r give
+// K S K^T = U U^T, K r = U z and chi2 = |z|^2, i.e. with
+// w0 = 1/sqrt(S00) and w1 = 1/sqrt(S00 det S),
+//   u0 = a w0,  u1 = (b S00 - a S01) w1,  z0 = r0 w0,  z1 = (r1 S00 - r0 S01) w1,
+//   p += u0 z0 + u1 z1,  C -= u0 u0^T + u1 u1^T,  chi2 = z0^2 + z1^2.
+// Only the two columns of U stay live through the covariance update (the
+// gain form keeps a, b and both columns of K).
 //
 // FP32 note (COMPENSATED): with the p2z measurement (x, y) the columns a and
-// b are strongly correlated and so is S, so K = [a b] S^-1 cancels.  K is
-// then formed as [a S11 - b S01, b S00 - a S01] / det with the rounding error
-// of each second product recovered by an FMA (and det by Kahan's 2x2
-// determinant); forming S^-1 first loses up to ~1e-4 relative accuracy in the
-// 1/pT variance after 20 layers.  The p2r measurement directions (azimuthal,
-// z) are nearly uncorrelated and need no compensation.
+// b are strongly correlated and so is S, so b S00 - a S01 and det S cancel;
+// both are then formed with the rounding error of the second product
+// recovered by an FMA (Kahan's 2x2 determinant).  Without it the 1/pT
+// variance loses up to ~1e-4 relative accuracy after 20 layers.  The p2r
+// measurement directions (azimuthal, z) are nearly uncorrelated and need no
+// compensation.
+template <bool COMPENSATED, class T>
+struct Sqrt2 {
+  T S00, S01, w0, w1;
+  __device__ __forceinline__ Sqrt2(T s00, T s01, T s11) : S00(s00), S01(s01) {
+    T det;
+    if (COMPENSATED) {
+      const T w01 = S01 * S01;
+      det = fma(S00, s11, -w01) - fma(S01, S01, -w01);
+    } else {
+      det = fma(S00, s11, -(S01 * S01));
+    }
+    w0 = frsqrt(S00);
+    w1 = frsqrt(S00 * det);
+  }
+  // x S00 - y S01, with the rounding error of y S01 recovered when compensated
+  __device__ __forceinline__ T cross(T x, T y) const {
+    if (COMPENSATED) {
+      const T t = y * S01;
+      return fma(x, S00, -t) - fma(y, S01, -t);
+    }
+    return fma(x, S00, -(y * S01));
+  }
+  // chi2 = |z|^2 of the residual r
+  __device__ __forceinline__ T chi2(T r0, T r1, T& z0, T& z1) const {
+    z0 = r0 * w0;
+    z1 = cross(r1, r0) * w1;
+    return fma(z0, z0, z1 * z1);
+  }
+};
+
 template <bool COMPENSATED, class T>
 __device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], const T (&b)[6],
                                        T S00, T S01, T S11, T r0, T r1) {
-  T k0[6], k1[6], id;
-  if (COMPENSATED) {
-    const T w01 = S01 * S01;
-    const T det = fma(S00, S11, -w01) - fma(S01, S01, -w01);
-    id = fdiv(T(1.f), det);
+  const Sqrt2<COMPENSATED, T> q(S00, S01, S11);
+  T z0, z1;
+  const T chi2 = q.chi2(r0, r1, z0, z1);
+  T u0[6], u1[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      const T t0 = b[i] * S01, t1 = a[i] * S01;
-      k0[i] = (fma(a[i], S11, -t0) - fma(b[i], S01, -t0)) * id;
-      k1[i] = (fma(b[i], S00, -t1) - fma(a[i], S01, -t1)) * id;
-    }
-  } else {
-    id = fdiv(T(1.f), fma(S00, S11, -(S01 * S01)));
-    const T i00 = S11 * id, i01 = -(S01 * id), i11 = S00 * id;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      k0[i] = fma(a[i], i00, b[i] * i01);
-      k1[i] = fma(a[i], i01, b[i] * i11);
-    }
+  for (int i = 0; i < 6; ++i) {
+    u0[i] = a[i] * q.w0;
+    u1[i] = q.cross(b[i], a[i]) * q.w1;
+    p[i] = fma(u0[i], z0, fma(u1[i], z1, p[i]));
   }
-#pragma unroll
-  for (int i = 0; i < 6; ++i) p[i] = fma(k0[i], r0, fma(k1[i], r1, p[i]));
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j) c[sym(i, j)] = fma(-k0[i], a[j], fma(-k1[i], b[j], c[sym(i, j)]));
-  // chi2 = (S11 r0^2 - 2 S01 r0 r1 + S00 r1^2) / det
-  return fma(S11 * r0, r0, fma(S00 * r1, r1, T(-2.f) * S01 * r0 * r1)) * id;
+    for (int j = 0; j <= i; ++j) c[sym(i, j)] = fma(-u0[i], u0[j], fma(-u1[i], u1[j], c[sym(i, j)]));
+  return chi2;
 }
 
 // After an update: carry cos/sin of phi and theta through the change of the
@@ -691,11 +812,8 @@ template <class T>
 __device__ __forceinline__ T chi2_z(const T (&p)[6], const T (&c)[21], const T (&m)[3],
                                     const T (&v)[6]) {
   const T S00 = c[sym(0, 0)] + v[0], S01 = c[sym(1, 0)] + v[1], S11 = c[sym(1, 1)] + v[2];
-  const T r0 = m[0] - p[0], r1 = m[1] - p[1];
-  const T w01 = S01 * S01;
-  const T det = fma(S00, S11, -w01) - fma(S01, S01, -w01);
-  const T id = fdiv(T(1.f), det);
-  return fma(S11 * r0, r0, fma(S00 * r1, r1, T(-2.f) * S01 * r0 * r1)) * id;
+  T z0, z1;
+  return Sqrt2<true, T>(S00, S01, S11).chi2(m[0] - p[0], m[1] - p[1], z0, z1);
 }
 template <class T>
 __device__ __forceinline__ T chi2_r(const T (&p)[6], const T (&c)[21], const T (&m)[3],
@@ -712,8 +830,8 @@ __device__ __forceinline__ T chi2_r(const T (&p)[6], const T (&c)[21], const T (
   const T S11 = c[sym(2, 2)] + v[5];
   const T r0 = fma(ch, m[1] - p[1], -(sh * (m[0] - p[0])));
   const T r1 = m[2] - p[2];
-  const T id = fdiv(T(1.f), fma(S00, S11, -(S01 * S01)));
-  return fma(S11 * r0, r0, fma(S00 * r1, r1, T(-2.f) * S01 * r0 * r1)) * id;
+  T z0, z1;
+  return Sqrt2<false, T>(S00, S01, S11).chi2(r0, r1, z0, z1);
 }
 
 }  // namespace fitk

@@ -62,6 +62,21 @@ def scaled_errors(gpu: dict, ref: dict, rtol: float = RTOL, chi2_abs: float = CH
             "par_each": e_par, "cov_each": e_cov}
 
 
+def strict_chi2_rate(gpu: dict, ref: dict) -> float:
+    """Fraction of the tracks neither side flagged whose summed chi2 agrees
+    to 1e-4 relative with a floor of 1e-3 on the tolerance,
+    |d chi2| <= max(1e-4 chi2, 1e-3): the fit's specified chi2 criterion
+    taken literally, without the FP32 residual-rounding term of CHI2_ABS.
+    Reported beside check() so that a loss of chi2 accuracy shows even where
+    it stays within the looser bound."""
+    ok = (np.asarray(gpu["status"]) == 0) & (np.asarray(ref["status"]) == 0)
+    c_g = np.asarray(gpu["chi2"], np.float64)[ok]
+    c_r = np.asarray(ref["chi2"], np.float64)[ok]
+    if not ok.any():
+        return 1.0
+    return float(np.mean(np.abs(c_g - c_r) <= np.maximum(RTOL * np.abs(c_r), 1e-3)))
+
+
 def check(gpu: dict, ref: dict, label: str = "", rtol: float = RTOL,
           chi2_abs: float = CHI2_ABS) -> dict:
     """Asserts parity on every track that neither side flagged; returns a summary."""

@@ -26,6 +26,11 @@ if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts t
 import gpu_util  # noqa: E402
 
 REL, FLOOR = 1e-3, 2e-3
+# Lowest accepted pass rates under the plain 1e-3-relative criterion
+# (regression guards; on a GB300: tracks 0.997 (p2r) and 1.000 (p2z),
+# components 0.919 and 0.952, the rest within the FP32 floor above).
+STRICT_TRACK_RATE_MIN = 0.99
+STRICT_COMPONENT_RATE_MIN = 0.90
 
 
 def _setup(mode, n, seed):
@@ -71,6 +76,16 @@ def test_gradient_matches_oracle(mode):
     scale = np.maximum(np.abs(ref["g_hpos"]).max(axis=(0, 1)), np.abs(ref["g_par0"]).max(axis=0))
     _assert_close(g_h, ref["g_hpos"], scale[None, None, :], "hit gradient")
     _assert_close(g_p, ref["g_par0"], scale[None, :], "initial-parameter gradient")
+    # the plain 1e-3-relative criterion: the fraction of tracks whose every
+    # gradient component is within 1e-3 of the track's gradient scale, and
+    # the fraction of components within 1e-3 of their own magnitude
+    dev = np.maximum(np.abs(g_h - ref["g_hpos"]).max(axis=(0, 1)),
+                     np.abs(g_p - ref["g_par0"]).max(axis=0))
+    track_rate = float(np.mean(dev <= 1e-3 * scale))
+    comp = np.concatenate([(np.abs(g_h - ref["g_hpos"]) <= 1e-3 * np.abs(ref["g_hpos"])).ravel(),
+                           (np.abs(g_p - ref["g_par0"]) <= 1e-3 * np.abs(ref["g_par0"])).ravel()])
+    print(f"mode {mode}: 1e-3 relative: tracks {track_rate:.4f}, components {comp.mean():.4f}")
+    assert track_rate >= STRICT_TRACK_RATE_MIN and comp.mean() >= STRICT_COMPONENT_RATE_MIN
     if mode == inputs.MODE_Z:
         assert (g_h[:, 2] == 0).all()  # a plane's hit z does not enter the fit
     f.close()

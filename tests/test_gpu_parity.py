@@ -20,6 +20,13 @@ if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts t
 
 import gpu_util  # noqa: E402
 
+# Lowest accepted fraction of tracks whose chi2 meets the literal 1e-4
+# criterion (parity.strict_chi2_rate); the rest are within the FP32
+# residual-rounding bound of parity.check.  A regression guard: on a GB300
+# the kernels gave 0.969 (p2r) and 0.995 (p2z) at 1024 tracks, 0.971 and
+# 0.991 on the full-size sample.
+STRICT_CHI2_RATE_MIN = 0.95
+
 
 @pytest.mark.parametrize("mode", [inputs.MODE_R, inputs.MODE_Z], ids=["p2r", "p2z"])
 def test_parity_1x1024x20(mode):
@@ -28,6 +35,10 @@ def test_parity_1x1024x20(mode):
     r = oracle.fit_set(ts, want_layers=True)
     s = parity.check(gpu_util.trim(g, 0, ts.n), r, f"mode {mode}")
     assert s["compared"] == ts.n and s["flag_gpu"] == 0
+    # chi2 under the specified 1e-4-relative criterion taken literally
+    rate = parity.strict_chi2_rate(gpu_util.trim(g, 0, ts.n), r)
+    print(f"mode {mode}: strict chi2 pass rate {rate:.4f}")
+    assert rate >= STRICT_CHI2_RATE_MIN, rate
     assert g["sync"]["tracks"] == ts.n and g["sync"]["no_intersection"] == 0
     # per-layer chi2 within the same per-track chi2 tolerance, layer by layer
     d = np.abs(g["chi2_layer"][:, :ts.n] - r["chi2_layer"])
@@ -424,13 +435,30 @@ def test_full_size_100x9600x20_sampled(mode):
     assert (g["status"] == 0).all()
     assert np.isfinite(g["par"]).all() and np.isfinite(g["cov"]).all()
     assert ((g["par"][4] > -np.pi - 1e-6) & (g["par"][4] <= np.pi + 1e-6)).all()
-    assert (g["cov"][parity.DIAG[[0, 1, 3, 4, 5]]] > 0).all()
+    assert (g["cov"][parity.DIAG[[3, 4, 5]]] > 0).all()
+    # x and y variances: on a cylinder the variance along the radial direction
+    # is zero, so for a track crossing within ~1e-4 rad of the x (y) axis the
+    # true x (y) variance is ~1e-12 of the transverse one and FP32 rounding can
+    # put it on either side of zero; every such track must still agree with
+    # the oracle, and no variance may be negative beyond that rounding
+    vx, vy = g["cov"][parity.DIAG[0]], g["cov"][parity.DIAG[1]]
+    assert ((vx + vy) > 0).all()
+    assert (np.minimum(vx, vy) >= -1e-6 * (vx + vy)).all()
+    odd = np.nonzero((vx <= 0) | (vy <= 0))[0]
+    if len(odd):
+        parity.check(gpu_util.trim({k: v[..., odd] if isinstance(v, np.ndarray) else v
+                                    for k, v in g.items()}, 0, len(odd)),
+                     oracle.fit_set(ts.subset(odd)), "tracks with a non-positive x or y variance")
     # mean chi2 per layer of a consistent filter is 2 (chi2 with 2 d.o.f.)
     assert abs(g["chi2"].mean() / ts.nlayer - 2.0) < 0.02
     rng = np.random.default_rng(0)
     idx = np.unique(np.concatenate([[0, ntrk - 1, ntrk, ts.n - 1],
                                     rng.choice(ts.n, 3000, replace=False)]))
     sub = ts.subset(idx)
-    parity.check(gpu_util.trim({k: v[..., idx] if isinstance(v, np.ndarray) else v
-                                for k, v in g.items()}, 0, len(idx)),
-                 oracle.fit_set(sub), "full size sample")
+    gs = gpu_util.trim({k: v[..., idx] if isinstance(v, np.ndarray) else v
+                        for k, v in g.items()}, 0, len(idx))
+    rs = oracle.fit_set(sub)
+    parity.check(gs, rs, "full size sample")
+    rate = parity.strict_chi2_rate(gs, rs)
+    print(f"mode {mode}: full size sample, strict chi2 pass rate {rate:.4f}")
+    assert rate >= STRICT_CHI2_RATE_MIN, rate

@@ -5,12 +5,16 @@ memory while they run (an online trigger process that reserves its GPU memory
 at start-up, a plug-in inside a framework that owns the device memory).  It
 keeps its scratch (per-event counters, event offsets) in a fixed array inside
 the library, so it must give the same fit as the handle-based entry point on
-every call, and clear its counters between calls.  This file is collected
-last so that a run stopping at the first failure has run every other test.
+every call, and clear its counters between calls; the fit is also checked
+against the FP64 oracle, and the free device memory is checked to be
+unchanged by a call once the library's kernels are loaded.  This file is
+collected last so that a run stopping at the first failure has run every
+other test.
 """
 import numpy as np
 import pytest
 
+import oracle
 import parity
 from paper_2409_09228_gb300 import fit, inputs
 
@@ -58,19 +62,34 @@ def test_noalloc_matches_handle_path_on_two_calls():
     ref_np = {k: v.cpu().numpy()[..., :n] for k, v in ref.items() if v is not None}
     starts = np.concatenate([[0], np.cumsum(ntrk)])
 
+    # every output buffer exists before the first call, so that the free
+    # device memory measured around the second call sees only the library
+    outs = [{"par": torch.full((6, ld), float("nan"), device="cuda"),
+             "cov": torch.full((21, ld), float("nan"), device="cuda"),
+             "q": torch.zeros(ld, dtype=torch.int32, device="cuda"),
+             "chi2": torch.full((ld,), float("nan"), device="cuda"),
+             "status": torch.full((ld,), 255, dtype=torch.uint8, device="cuda")}
+            for _ in range(2)]
+    oracle_events = [oracle.fit_set(s) if s.n else None for s in sets]
     for call in range(2):
-        out = {"par": torch.full((6, ld), float("nan"), device="cuda"),
-               "cov": torch.full((21, ld), float("nan"), device="cuda"),
-               "q": torch.zeros(ld, dtype=torch.int32, device="cuda"),
-               "chi2": torch.full((ld,), float("nan"), device="cuda"),
-               "status": torch.full((ld,), 255, dtype=torch.uint8, device="cuda")}
+        out = outs[call]
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         per_event = fit.fit_propagate_update_noalloc(
             geom_r, geom_z, *dev_in, ntrk, modes, par_out=out["par"], cov_out=out["cov"],
             q_out=out["q"], chi2=out["chi2"], status=out["status"])
+        torch.cuda.synchronize()
+        if call == 1:  # the first call may load the library's kernels; the second allocates nothing
+            assert torch.cuda.mem_get_info()[0] == free_before
         got = {k: v.cpu().numpy()[..., :n] for k, v in out.items()}
         # same outputs as the handle path, within the parity tolerance
         s = parity.check(got, ref_np, f"no-alloc call {call}")
         assert s["compared"] == int((ref_np["status"] == 0).sum())
+        # and the same fit as the FP64 oracle, event by event
+        for e, ref_e in enumerate(oracle_events):
+            if ref_e is not None:
+                sub = {k: v[..., starts[e]:starts[e + 1]] for k, v in got.items()}
+                parity.check(sub, ref_e, f"no-alloc call {call} event {e} vs oracle")
         assert np.array_equal(got["status"], ref_np["status"])
         assert np.array_equal(got["q"], ref_np["q"])
         # per-event counters: fresh on each call and consistent with the statuses
