@@ -122,6 +122,18 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
   const float* hp = a.hpos + t;
   const float* hc = a.hcov + t;
   const int64_t ldh = a.ld_hit;
+  // lanes that hit max_iter or flipped charge on some layer; the status bits
+  // (with non-finite for lanes no longer alive) are set once, on return
+  M any_nc = fitk::lt(T(1.f), T(0.f)), any_flip = any_nc;
+  auto done = [&](int r) {
+#pragma unroll
+    for (int i = 0; i < Lanes<T>::n; ++i) {
+      if (Lanes<T>::get(any_nc, i)) st[i] |= FIT_ST_NOT_CONVERGED;
+      if (Lanes<T>::get(any_flip, i)) st[i] |= FIT_ST_CHARGE_FLIP;
+      if (!Lanes<T>::get(alive, i)) st[i] |= FIT_ST_NONFINITE;
+    }
+    return r;
+  };
   for (int l = l0; l < a.nlayer; ++l) {
     T m[3], v[6];
 #pragma unroll
@@ -138,17 +150,13 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
     else
       fail = fitk::prop_r(s.p, s.c, s.g, dkdw, sf, geo.max_iter, geo.tol * sf,
                           geo.line_start, iters, nc);
-    if (fitk::any(fitk::and_(fail, alive))) return l;
+    if (fitk::any(fitk::and_(fail, alive))) return done(l);
     const T phi_pred = s.p[4], th_pred = s.p[5];
     T x2 = (MODE == FIT_MODE_Z) ? fitk::update_z(s.p, s.c, m, v) : fitk::update_r(s.p, s.c, m, v);
     const M flip = fitk::normalise(s.p, s.c, s.qf, s.g, phi_pred, th_pred);
     alive = fitk::and_(alive, fitk::finite_(x2));
-#pragma unroll
-    for (int i = 0; i < Lanes<T>::n; ++i) {
-      if (Lanes<T>::get(nc, i)) st[i] |= FIT_ST_NOT_CONVERGED;
-      if (Lanes<T>::get(flip, i)) st[i] |= FIT_ST_CHARGE_FLIP;
-      if (!Lanes<T>::get(alive, i)) st[i] |= FIT_ST_NONFINITE;
-    }
+    any_nc = fitk::or_(any_nc, nc);
+    any_flip = fitk::or_(any_flip, flip);
     x2 = fitk::sel(alive, x2, T(0.f));
     s.chi2 += x2;
     if (a.chi2_layer) fitk::st(a.chi2_layer + ix<L>(l, t, a.ld_out, a.nlayer), x2);
@@ -156,17 +164,17 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
       if (a.chi2_layer)
         for (int r = l + 1; r < a.nlayer; ++r)
           fitk::st(a.chi2_layer + ix<L>(r, t, a.ld_out, a.nlayer), T(0.f));
-      return a.nlayer;
+      return done(a.nlayer);
     }
     // A packed lane that turned non-finite would fail every later
     // propagation, and a propagation that fails for any lane is applied to
     // none: the pair splits at the next layer, where the live track goes on
     // alone and the dead one is only stored.
     if constexpr (Lanes<T>::n > 1) {
-      if (!fitk::all(alive)) return l + 1;
+      if (!fitk::all(alive)) return done(l + 1);
     }
   }
-  return a.nlayer;
+  return done(a.nlayer);
 }
 
 // One track alone from layer l0 to the end (or to a surface it cannot

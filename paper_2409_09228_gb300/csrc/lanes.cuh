@@ -40,18 +40,27 @@ __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a,
 __device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
 
 // Division and square root where a couple of ulp are far below the fit's
-// tolerance: the approximate reciprocal and rsqrt (MUFU) instead of the IEEE
-// sequences.
+// tolerance: the approximate reciprocal, square root and rsqrt (MUFU) instead
+// of the IEEE sequences.
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ F2 fdiv(F2 a, F2 b) {
   return F2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y));
 }
-__device__ __forceinline__ float fsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+// Approximate square root (one MUFU operation, relative error ~2^-23); NaN
+// for x < 0, which every caller either excludes by its own test or sends
+// down a failing branch.
+__device__ __forceinline__ float fsqrt(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ F2 fsqrt(F2 x) { return F2(fsqrt(x.v.x), fsqrt(x.v.y)); }
 __device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ F2 frsqrt(F2 x) { return F2(rsqrtf(x.v.x), rsqrtf(x.v.y)); }
 __device__ __forceinline__ float fabs_(float x) { return fabsf(x); }
 __device__ __forceinline__ F2 fabs_(F2 x) { return F2(fabsf(x.v.x), fabsf(x.v.y)); }
+__device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ F2 fmax_(F2 a, F2 b) { return F2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
 __device__ __forceinline__ float floor_(float x) { return floorf(x); }
 __device__ __forceinline__ F2 floor_(F2 x) { return F2(floorf(x.v.x), floorf(x.v.y)); }
 __device__ __forceinline__ float copysign_(float a, float b) { return copysignf(a, b); }
@@ -88,6 +97,7 @@ __device__ __forceinline__ double fsqrt(double x) { return x > 0.0 ? ::sqrt(x) :
 __device__ __forceinline__ double frsqrt(double x) { return 1.0 / ::sqrt(x); }
 __device__ __forceinline__ double fabs_(double x) { return ::fabs(x); }
 __device__ __forceinline__ double floor_(double x) { return ::floor(x); }
+__device__ __forceinline__ double fmax_(double a, double b) { return ::fmax(a, b); }
 __device__ __forceinline__ double copysign_(double a, double b) { return ::copysign(a, b); }
 __device__ __forceinline__ bool le(double a, double b) { return a <= b; }
 __device__ __forceinline__ bool lt(double a, double b) { return a < b; }

@@ -142,6 +142,32 @@ __device__ __forceinline__ F2 sinc_deriv(F2 u, F2 s, F2 cu) {
   return F2(sinc_deriv(u.v.x, s.v.x, cu.v.x), sinc_deriv(u.v.y, s.v.y, cu.v.y));
 }
 
+// sin(u)/u, cos(u) and the derivative of sin(u)/u with one range test.
+__device__ __forceinline__ void sinc_cs(float u, float& s, float& cu, float& sp) {
+  const float au = fabsf(u);
+  if (au <= 1.25f) {
+    const bool shortform = au <= 0.1f;
+    sinc_series(u * u, s, cu, shortform);
+    sp = sinc_deriv_series(u, shortform);
+  } else {
+    float sn;
+    sincos_cw(u, sn, cu);
+    s = fdiv(sn, u);
+    sp = fdiv(cu - s, u);
+  }
+}
+__device__ __forceinline__ void sinc_cs(F2 u, F2& s, F2& cu, F2& sp) {
+  const F2 au = fabs_(u);
+  if (all(le(au, F2(1.25f)))) {
+    const bool shortform = all(le(au, F2(0.1f)));
+    sinc_series(u * u, s, cu, shortform);
+    sp = sinc_deriv_series(u, shortform);
+  } else {
+    sinc_cs(u.v.x, s.v.x, cu.v.x, sp.v.x);
+    sinc_cs(u.v.y, s.v.y, cu.v.y, sp.v.y);
+  }
+}
+
 // (c, s) <- (cos(a + d), sin(a + d)) from (c, s) = (cos a, sin a), given
 // (cd, sd) = (cos d, sin d).
 template <class T>
@@ -194,6 +220,30 @@ __device__ __forceinline__ void turn_by(double& c, double& s, double d) {
   double sd, cd;
   ::sincos(d, &sd, &cd);
   turn(c, s, cd, sd);
+}
+__device__ __forceinline__ void sinc_cs(double u, double& s, double& cu, double& sp) {
+  sinc_c(u, s, cu);
+  sp = sinc_deriv(u, s, cu);
+}
+
+// Two turns by small angles (as turn_by) with one range test.
+template <class T>
+__device__ __forceinline__ void turn_by2(T& c1, T& s1, T d1, T& c2, T& s2, T d2) {
+  if (all(le(fmax_(fabs_(d1), fabs_(d2)), T(0.1f)))) {
+    const T q1 = d1 * d1, q2 = d2 * d2;
+    turn(c1, s1, fma(q1, fma(q1, T(4.1666667e-02f), T(-0.5f)), T(1.0f)),
+         d1 * fma(q1, fma(q1, T(8.3333333e-03f), T(-1.6666667e-01f)), T(1.0f)));
+    turn(c2, s2, fma(q2, fma(q2, T(4.1666667e-02f), T(-0.5f)), T(1.0f)),
+         d2 * fma(q2, fma(q2, T(8.3333333e-03f), T(-1.6666667e-01f)), T(1.0f)));
+  } else {
+    turn_by(c1, s1, d1);
+    turn_by(c2, s2, d2);
+  }
+}
+__device__ __forceinline__ void turn_by2(double& c1, double& s1, double d1, double& c2, double& s2,
+                                         double d2) {
+  turn_by(c1, s1, d1);
+  turn_by(c2, s2, d2);
 }
 
 // Cosine and sine of phi and theta, carried with the track.
@@ -391,9 +441,8 @@ __device__ __forceinline__ typename Lanes<T>::M prop_z(T (&p)[6], T (&c)[21], Tr
   if (any(fail)) return fail;
   const T kappa = dkdw * p[3];
   const T u = T(0.5f) * kappa * h;
-  T s, cu;
-  sinc_c(u, s, cu);
-  const T sp = sinc_deriv(u, s, cu);
+  T s, cu, sp;
+  sinc_cs(u, s, cu, sp);
   const T su = u * s;  // sin(u)
   T cm = g.cphi, sm = g.sphi;
   turn(cm, sm, cu, su);  // phi + u
@@ -521,7 +570,7 @@ enum class Start { kAuto, kFast, kGiven };
 // The helix quantities of path_r's last evaluation.
 template <class T>
 struct PathR {
-  T h, d, u, s, cu, cm, sm, px, py, c1, s1;
+  T h, d, u, s, cu, sp, cm, sm, px, py, c1, s1;
 };
 
 // Path length to the cylinder r = R by straight-line steps along the current
@@ -593,13 +642,13 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
   // outside the loop (from the closed-form crossing it is almost always the
   // only one, and peeled it is 3 % faster); max_iter >= 1.
   M conv = lt(T(1.f), T(0.f));  // all false
-  T u = T(0.f), s = T(1.f), cu = T(1.f), sm = sph, cm = cph, px = x, py = y, c1 = cph, s1 = sph,
-    d = T(0.f);
+  T u = T(0.f), s = T(1.f), cu = T(1.f), sp = T(0.f), sm = sph, cm = cph, px = x, py = y, c1 = cph,
+    s1 = sph, d = T(0.f);
   auto step = [&]() {
 #pragma unroll
     for (int i = 0; i < Lanes<T>::n; ++i) iters[i] += Lanes<T>::get(conv, i) ? 0u : 1u;
     u = T(0.5f) * kappa * h;
-    sinc_c(u, s, cu);
+    sinc_cs(u, s, cu, sp);
     const T su = u * s;
     cm = cph;
     sm = sph;
@@ -623,7 +672,7 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
   step();
   for (int it = 1; it < max_iter && !all(conv); ++it) step();
   notconv = not_(conv);
-  w = {h, d, u, s, cu, cm, sm, px, py, c1, s1};
+  w = {h, d, u, s, cu, sp, cm, sm, px, py, c1, s1};
   return fail;
 }
 
@@ -643,14 +692,13 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
   const auto fail = path_r<T, SEEDED, START>(p, g, kappa, R, max_iter, tol_abs, line_start,
                                              iters, notconv, w, gseed, h_given);
   if (any(fail)) return fail;
-  const T h = w.h, d = w.d, u = w.u, s = w.s, cu = w.cu, cm = w.cm, sm = w.sm;
+  const T h = w.h, d = w.d, s = w.s, sp = w.sp, cm = w.cm, sm = w.sm;
   T px = w.px, py = w.py, c1 = w.c1, s1 = w.s1;
   // The loop evaluated the helix at h - d; move along the tangent by d
   // (the neglected curvature term, kappa d^2 / 2, is below FP32 resolution
   // once |d| <= tol) and turn the direction by kappa d.
   px = fma(d, c1, px);
   py = fma(d, s1, py);
-  const T sp = sinc_deriv(u, s, cu);
   const T isth = fdiv(T(1.f), g.sth);
   const T cot = g.cth * isth;
   const T dx = px - x, dy = py - y;
@@ -733,10 +781,12 @@ __device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], c
   T z0, z1;
   const T chi2 = q.chi2(r0, r1, z0, z1);
   T u0[6], u1[6];
+  // uncompensated: u1 = b (S00 w1) - a (S01 w1)
+  const T al = q.S00 * q.w1, be = q.S01 * q.w1;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     u0[i] = a[i] * q.w0;
-    u1[i] = q.cross(b[i], a[i]) * q.w1;
+    u1[i] = COMPENSATED ? q.cross(b[i], a[i]) * q.w1 : fma(b[i], al, -(a[i] * be));
     p[i] = fma(u0[i], z0, fma(u1[i], z1, p[i]));
   }
 #pragma unroll
@@ -753,8 +803,7 @@ __device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], c
 template <class T>
 __device__ __forceinline__ typename Lanes<T>::M normalise(T (&p)[6], T (&c)[21], T& qf,
                                                           Trig<T>& g, T phi_before, T th_before) {
-  turn_by(g.cphi, g.sphi, p[4] - phi_before);
-  turn_by(g.cth, g.sth, p[5] - th_before);
+  turn_by2(g.cphi, g.sphi, p[4] - phi_before, g.cth, g.sth, p[5] - th_before);
   const T k = floor_((pi_<T>() - p[4]) * inv_two_pi_<T>());
   p[4] = fma(k, two_pi_<T>(), p[4]);
   const auto flip = lt(p[3], T(0.f));
