@@ -1000,18 +1000,28 @@ def main():
                                       cov_out=o["cov"], q_out=o["q"], chi2=o["chi2"],
                                       status=o["status"], stream=stream)
 
-    e2e_ms = float("nan")
-    if args.e2e_steps > 0:
-        e2e_step()
+    def e2e_mapped_step():
+        o = pinned_out
+        fit.fit_propagate_update_mapped(f.h, *pinned_in, ntrk_both, mode_both, par_out=o["par"],
+                                        cov_out=o["cov"], q_out=o["q"], chi2=o["chi2"],
+                                        status=o["status"], stream=stream)
+
+    def time_e2e(fn):
+        fn()
         torch.cuda.synchronize(dev)
         barrier(world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.e2e_steps):
-            e2e_step()
+            fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        e2e_ms = max_over_ranks(world, e0.elapsed_time(e1) / args.e2e_steps)
+        return max_over_ranks(world, e0.elapsed_time(e1) / args.e2e_steps)
+
+    e2e_ms = {"staged": float("nan"), "mapped": float("nan")}
+    if args.e2e_steps > 0:
+        e2e_ms["staged"] = time_e2e(e2e_step)
+        e2e_ms["mapped"] = time_e2e(e2e_mapped_step)
     f.sync(stream)
     f.close()
 
@@ -1040,11 +1050,17 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded generator, paper Sec. 3.1 smearing)",
             "config": config_dict(args), "roofline": roof, "clocks": clk,
-            "e2e": {"value": world * units_per_step / (e2e_ms / 1e3), "unit": "track-layer/s",
+            "e2e": {"value": world * units_per_step / (min(e2e_ms.values()) / 1e3),
+                    "unit": "track-layer/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "path": "one fit_propagate_update_host call per step on page-locked host "
-                            "buffers holding both modes (chunked copies in, fit, copies out, "
-                            "three streams)"},
+                    "path": min(e2e_ms, key=e2e_ms.get),
+                    "paths": {"staged": "one fit_propagate_update_host call per step on "
+                                        "page-locked host buffers holding both modes (chunked "
+                                        "copies in, fit, copies out, three streams)",
+                              "mapped": "one fit_propagate_update_mapped call per step: the "
+                                        "fused kernels read the page-locked inputs and write the "
+                                        "outputs over the host link, no staging copies"},
+                    "ms_per_step": e2e_ms},
             "gpu_launches": 2 * args.steps, "p2r_iterations_per_track_layer": it_per,
             "p2r_straight_line_start": line_start}
     if world == 1 and not args.no_cpu_baseline:

@@ -427,6 +427,25 @@ int fit_propagate_update_host(fit_handle* h, const fit_tracks_in* in, const fit_
                               const int32_t* mode, void* stream);
 
 /*
+ * fit_propagate_update_mapped: fit_propagate_update on page-locked HOST
+ * buffers that the fused kernel reads and writes in place, over the host
+ * link, without staging copies (zero-copy; on a Grace host the NVLink-C2C
+ * link).  Same structs, layouts, checks and results as fit_propagate_update
+ * (bit-identical: the same kernels run on the same values).  Every data
+ * pointer must lie in page-locked host memory (cudaHostAlloc, or
+ * cudaHostRegister'ed) that the handle's device reaches under the same
+ * address; each is checked with cudaPointerGetAttributes and a pointer that
+ * is not returns FIT_ERR_ARG before anything runs.  Asynchronous on `stream`:
+ * the host buffers must stay valid, and the outputs unread, until the stream
+ * passes the call (fit_sync).  Allocates nothing.  This is the host-path
+ * counterpart of the paper's transfer measurement (Sec. 3.1, Sec. 5) for a
+ * device that shares a coherent link with its host.
+ */
+int fit_propagate_update_mapped(fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
+                                const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
+                                const int32_t* mode, void* stream);
+
+/*
  * Learned path-length seed for p2r.  The paper's p2r finds the path length to
  * the cylinder by discrete straight-line steps (Sec. 3.2); these entry points
  * add a small network, 8 -> 64 -> 64 -> 1 with ReLU, BF16 weights and FP32

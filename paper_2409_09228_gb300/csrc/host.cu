@@ -205,3 +205,43 @@ extern "C" int fit_propagate_update_host(fit_handle* h, const fit_tracks_in* in,
   h->tracks += (uint64_t)total;
   return FIT_OK;
 }
+
+namespace {
+
+// Whether p lies in page-locked host memory that the current device reaches
+// under the same address (so a kernel may dereference it).
+bool mapped_host(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of a pointer CUDA does not know
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
+}  // namespace
+
+extern "C" int fit_propagate_update_mapped(fit_handle* h, const fit_tracks_in* in,
+                                           const fit_tracks_out* out, const fit_hits* hits,
+                                           int nevt, const int64_t* ntrk, int nlayer,
+                                           const int32_t* mode, void* stream) {
+  static const char* kWho = "fit_propagate_update_mapped";
+  g_last_error.clear();
+  if (!h) return fail(FIT_ERR_ARG, std::string(kWho) + ": NULL handle");
+  int64_t total = 0;
+  int rc = check_call(h, in, out, hits, nevt, ntrk, nlayer, mode, &total, kWho);
+  if (rc != FIT_OK || total == 0) return rc;
+  DeviceGuard guard(h->device);
+  const void* ptrs[] = {in->par, in->cov, in->q, out->par, out->cov, out->q, out->chi2,
+                        out->chi2_layer, out->status, hits->pos, hits->cov};
+  for (const void* p : ptrs)
+    if (p && !mapped_host(p))
+      return fail(FIT_ERR_ARG, std::string(kWho) +
+                                   ": a buffer is not page-locked host memory mapped into the "
+                                   "device's address space");
+  rc = run_fit(h, base_args(in, out, hits, nlayer, h->d_counters), nevt, ntrk, mode, kWho,
+               static_cast<cudaStream_t>(stream));
+  if (rc != FIT_OK) return rc;
+  h->tracks += (uint64_t)total;
+  return FIT_OK;
+}

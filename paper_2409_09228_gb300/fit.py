@@ -97,7 +97,7 @@ EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_l
            "fit_adjoint_backward", "fit_mlp_create", "fit_mlp_destroy", "fit_mlp_set_params",
            "fit_mlp_get_params", "fit_mlp_prepare", "fit_mlp_forward", "fit_mlp_gradient",
            "fit_mlp_adam_step", "fit_mlp_train", "fit_mlp_attach", "fit_path_lengths",
-           "fit_propagate_update_host", "fit_propagate_update_f64",
+           "fit_propagate_update_host", "fit_propagate_update_mapped", "fit_propagate_update_f64",
            "fit_propagate_update_layout", "fit_find_tracks", "fit_find_tracks_f64")
 FIT_LAYOUT_SOA = 0
 FIT_LAYOUT_AOSOA32 = 1
@@ -186,6 +186,8 @@ def load(build_if_missing: bool = True):
     L.fit_propagate_update_f64.restype = ctypes.c_int
     L.fit_propagate_update_host.argtypes = L.fit_propagate_update.argtypes
     L.fit_propagate_update_host.restype = ctypes.c_int
+    L.fit_propagate_update_mapped.argtypes = L.fit_propagate_update.argtypes
+    L.fit_propagate_update_mapped.restype = ctypes.c_int
     i32p = ctypes.POINTER(ctypes.c_int32)
     L.fit_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_uint64]
     L.fit_mlp_create.restype = ctypes.c_int
@@ -360,7 +362,7 @@ def _hptr(a) -> Optional[int]:
         return None
     if hasattr(a, "data_ptr"):
         if a.is_cuda:
-            raise ValueError("fit_propagate_update_host takes host arrays")
+            raise ValueError("the host entry points take host arrays")
         return a.data_ptr()
     return np.asarray(a).ctypes.data
 
@@ -382,6 +384,28 @@ def fit_propagate_update_host(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Se
     nt = np.ascontiguousarray(ntrk, dtype=np.int64)
     md = np.ascontiguousarray(mode, dtype=np.int32)
     _check(L.fit_propagate_update_host(
+        ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
+        nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), hpos.shape[0],
+        md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))
+
+
+def fit_propagate_update_mapped(h: int, par_in, cov_in, q_in, hpos, hcov, ntrk: Sequence[int],
+                                mode: Sequence[int], par_out=None, cov_out=None, q_out=None,
+                                chi2=None, chi2_layer=None, status=None, stream=None) -> None:
+    """The fused fit reading and writing page-locked HOST tensors in place
+    (zero-copy over the host link); the tensors must stay alive, and the
+    outputs unread, until the stream passes the call (fit_sync)."""
+    L = load()
+    par_out = par_in if par_out is None else par_out
+    cov_out = cov_in if cov_out is None else cov_out
+    q_out = q_in if q_out is None else q_out
+    tin = fit_tracks_in(_hptr(par_in), _hptr(cov_in), _hptr(q_in), par_in.shape[-1])
+    tout = fit_tracks_out(_hptr(par_out), _hptr(cov_out), _hptr(q_out), _hptr(chi2),
+                          _hptr(chi2_layer), _hptr(status), par_out.shape[-1])
+    hits = fit_hits(_hptr(hpos), _hptr(hcov), hpos.shape[-1])
+    nt = np.ascontiguousarray(ntrk, dtype=np.int64)
+    md = np.ascontiguousarray(mode, dtype=np.int32)
+    _check(L.fit_propagate_update_mapped(
         ctypes.c_void_p(h), ctypes.byref(tin), ctypes.byref(tout), ctypes.byref(hits), len(nt),
         nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), hpos.shape[0],
         md.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)))

@@ -106,3 +106,42 @@ def test_host_path_argument_errors():
             fit.fit_propagate_update_host(f.h, d, *hin[1:], ev.ntrk, ev.mode)
     finally:
         f.close()
+
+
+def test_mapped_path_is_bit_identical_and_checks_its_pointers():
+    """fit_propagate_update_mapped: the fused kernels read the tracks and hits
+    from page-locked host memory and write the outputs there, with no staging
+    copy.  Same kernels on the same values: bit-identical to the device path.
+    Pageable or device buffers are refused before anything runs."""
+    ev = _events(9, 29, 4000.0)
+    n = ev.n
+    ld = gpu_util.pad_ld(n) + 4
+    f = fit.Fitter(fit.Geometry(ev.B, ev.surf[0]), fit.Geometry(ev.B, ev.surf[1]))
+    try:
+        d = [gpu_util.to_dev(a, ld) for a in (ev.par0, ev.cov0, ev.q, ev.hpos, ev.hcov)]
+        dev = f.run(*d, ev.ntrk, ev.mode, layers=True)
+        st_dev = f.sync()
+        hin = _host(ev, ld, True)
+        hout = _host_out(n, ld, 20, True)
+        outs = dict(par_out=hout["par"], cov_out=hout["cov"], q_out=hout["q"], chi2=hout["chi2"],
+                    chi2_layer=hout["chi2_layer"], status=hout["status"])
+        fit.fit_propagate_update_mapped(f.h, *hin, ev.ntrk, ev.mode, **outs)
+        st_map = f.sync()
+        for k in ("par", "cov", "q", "chi2", "chi2_layer", "status"):
+            a, b = dev[k].cpu().numpy()[..., :n], _np(hout[k], n)
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), k
+        assert st_map == st_dev
+        # refused: a pageable input, a pageable output; the outputs stay untouched
+        before = hout["chi2"].clone()
+        pageable = [np.array(t.numpy()) for t in hin]
+        with pytest.raises(fit.FitError) as e:
+            fit.fit_propagate_update_mapped(f.h, pageable[0], *hin[1:], ev.ntrk, ev.mode, **outs)
+        assert e.value.code == fit.FIT_ERR_ARG and "page-locked" in str(e.value)
+        with pytest.raises(fit.FitError) as e:
+            fit.fit_propagate_update_mapped(f.h, *hin, ev.ntrk, ev.mode,
+                                            **{**outs, "chi2": torch.empty(ld).numpy()})
+        assert e.value.code == fit.FIT_ERR_ARG
+        torch.cuda.synchronize()
+        assert torch.equal(before, hout["chi2"])
+    finally:
+        f.close()
