@@ -216,13 +216,18 @@ int fit_propagate_update_noalloc(const fit_config* cfg_r, const fit_config* cfg_
  * those of fit_propagate_update on the same events.
  */
 typedef struct {
-  int threads_per_block; /* 32, 64 or 128 */
+  int threads_per_block; /* 32, 64, 128 or 256 (64, 128 or 256 with one track per thread) */
   int blocks_per_sm;     /* grid = blocks_per_sm x SM count; 0 = as many as fit */
   int persistent;        /* 1: one persistent launch; 0: one launch per run of
                             same-mode events (fit_propagate_update's form) */
   int tracks_per_thread; /* 2 (or 0, a zeroed struct): two tracks per thread in
                             packed f32x2 instructions; 1: one track per thread
                             (persistent form only) */
+  int layout;            /* how the plan reads the caller's track and hit arrays:
+                            FIT_LAYOUT_SOA (0, a zeroed struct) or
+                            FIT_LAYOUT_AOSOA32 (see fit_propagate_update_layout);
+                            at fit_plan_create also FIT_LAYOUT_TUNE: run as SoA
+                            until fit_plan_tune picks one of the two */
 } fit_launch_config;
 
 typedef struct {
@@ -254,14 +259,22 @@ int fit_plan_run(fit_plan* plan, const fit_tracks_in* in, const fit_tracks_out* 
                  const fit_hits* hits, void* stream);
 
 /*
- * fit_plan_tune: the autotuner.  Times every candidate launch shape (persistent
- * with two tracks per thread and 32, 64 or 128 threads per block, or one track
- * per thread and 64 or 128 threads per block, each at every resident-block
- * count; and the per-segment form) on these buffers -- out must not alias in, it is written --
- * and keeps the fastest.  A shape found before for the same device, depth and
- * event-size histogram (in this process, or in the text file cache_path if not
- * NULL) is reused without measuring; new results are appended to cache_path.
- * Waits for the stream.  The tuning runs do not count into the handle.
+ * fit_plan_tune: the autotuner (paper Sec. 5: hand-set launch parameters were
+ * worth ~30 %, registers per thread ~10 %).  Times every candidate launch
+ * shape -- persistent with two tracks per thread and 32, 64, 128 or 256 threads
+ * per block, or one track per thread and 64, 128 or 256 threads per block,
+ * each at every resident-block count, and the per-segment form -- on these
+ * buffers (out must not alias in; it is written) and keeps the fastest.  The
+ * buffers are in the plan's layout.  A plan created with FIT_LAYOUT_TUNE
+ * passes SoA buffers and has every shape timed in both layouts (the AoSoA runs
+ * read a converted copy of the inputs in scratch device memory, about 4 bytes
+ * x (54 + 10 nlayer) per track, allocated and freed by the call); afterwards
+ * the plan runs in the layout chosen (fit_plan_get_info) and fit_plan_run
+ * takes buffers in that layout (fit_relayout converts).  A shape found before
+ * for the same device, layout choice, depth and event-size histogram (in this
+ * process, or in the text file cache_path if not NULL) is reused without
+ * measuring; new results are appended to cache_path.  Waits for the stream.
+ * The tuning runs do not count into the handle.
  */
 int fit_plan_tune(fit_plan* plan, const fit_tracks_in* in, const fit_tracks_out* out,
                   const fit_hits* hits, void* stream, const char* cache_path);
@@ -271,6 +284,20 @@ int fit_plan_get_info(const fit_plan* plan, fit_plan_info* info);
 
 /* fit_plan_destroy: frees the plan (after its pending work ends). */
 void fit_plan_destroy(fit_plan* plan);
+
+/*
+ * fit_relayout: copies rows x n 4-byte elements (float or int32; component k
+ * of track t) from the DEVICE array src in layout src_layout (FIT_LAYOUT_SOA
+ * or FIT_LAYOUT_AOSOA32, leading dimension src_ld) into the DEVICE array dst
+ * in dst_layout (dst_ld); src and dst must not overlap.  For the track and
+ * hit arrays of a plan whose tuner chose AoSoA: par (rows 6), cov (21), hit
+ * positions (3 x nlayer), hit covariances (6 x nlayer), per-layer chi2
+ * (nlayer); arrays of one component per track (q, chi2, status) are the same
+ * in both layouts.  ld >= n, and a multiple of 32 in FIT_LAYOUT_AOSOA32.
+ * Asynchronous on `stream`.  Errors: FIT_ERR_ARG, FIT_ERR_CUDA.
+ */
+int fit_relayout(const void* src, int64_t src_ld, int src_layout, void* dst, int64_t dst_ld,
+                 int dst_layout, int rows, int64_t n, void* stream);
 
 /*
  * Gradient of each track's summed chi2 with respect to its hit positions and
@@ -325,6 +352,7 @@ int fit_adjoint_backward(fit_handle* h, const fit_hits* hits, int nevt, const in
  */
 #define FIT_LAYOUT_SOA 0
 #define FIT_LAYOUT_AOSOA32 1
+#define FIT_LAYOUT_TUNE 2 /* fit_plan_create only: let fit_plan_tune choose */
 int fit_propagate_update_layout(fit_handle* h, const fit_tracks_in* in, const fit_tracks_out* out,
                                 const fit_hits* hits, int nevt, const int64_t* ntrk, int nlayer,
                                 const int32_t* mode, int layout, void* stream);

@@ -72,7 +72,8 @@ class fit_status(ctypes.Structure):
 
 class fit_launch_config(ctypes.Structure):
     _fields_ = [("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("persistent", ctypes.c_int), ("tracks_per_thread", ctypes.c_int)]
+                ("persistent", ctypes.c_int), ("tracks_per_thread", ctypes.c_int),
+                ("layout", ctypes.c_int)]
 
 
 class fit_plan_info(ctypes.Structure):
@@ -98,9 +99,11 @@ EXPORTS = ("fit_init", "fit_propagate_update", "fit_sync", "fit_destroy", "fit_l
            "fit_mlp_get_params", "fit_mlp_prepare", "fit_mlp_forward", "fit_mlp_gradient",
            "fit_mlp_adam_step", "fit_mlp_train", "fit_mlp_attach", "fit_path_lengths",
            "fit_propagate_update_host", "fit_propagate_update_mapped", "fit_propagate_update_f64",
-           "fit_propagate_update_layout", "fit_find_tracks", "fit_find_tracks_f64")
+           "fit_propagate_update_layout", "fit_find_tracks", "fit_find_tracks_f64",
+           "fit_relayout", "fit_probe_fp32")
 FIT_LAYOUT_SOA = 0
 FIT_LAYOUT_AOSOA32 = 1
+FIT_LAYOUT_TUNE = 2
 FIT_MLP_INPUTS = 8
 FIT_MLP_HIDDEN = 64
 FIT_MLP_PARAMS = 4801
@@ -214,6 +217,8 @@ def load(build_if_missing: bool = True):
     L.fit_probe_fp32.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
                                  ctypes.POINTER(ctypes.c_double)]
     L.fit_probe_fp32.restype = ctypes.c_int
+    L.fit_relayout.argtypes = [vp, i64, ctypes.c_int, vp, i64, ctypes.c_int, ctypes.c_int, i64, vp]
+    L.fit_relayout.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -457,12 +462,13 @@ def _buffers(par_in, cov_in, q_in, hpos, hcov, par_out, cov_out, q_out, chi2, ch
 
 def fit_plan_create(h: int, ntrk: Sequence[int], mode: Sequence[int], nlayer: int,
                     threads_per_block: int = 128, blocks_per_sm: int = 0,
-                    persistent: bool = True, tracks_per_thread: int = 2) -> int:
+                    persistent: bool = True, tracks_per_thread: int = 2,
+                    layout: int = FIT_LAYOUT_SOA) -> int:
     """A plan for the batched persistent form (see fit.h)."""
     nt = np.ascontiguousarray(ntrk, dtype=np.int64)
     md = np.ascontiguousarray(mode, dtype=np.int32)
     cfg = fit_launch_config(threads_per_block, blocks_per_sm, int(persistent),
-                            int(tracks_per_thread))
+                            int(tracks_per_thread), int(layout))
     p = ctypes.c_void_p()
     _check(load().fit_plan_create(ctypes.c_void_p(h), len(nt),
                                   nt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
@@ -495,8 +501,21 @@ def fit_plan_get_info(plan: int) -> dict:
     c = info.config
     return {"threads_per_block": c.threads_per_block, "blocks_per_sm": c.blocks_per_sm,
             "persistent": bool(c.persistent), "tracks_per_thread": c.tracks_per_thread,
+            "layout": c.layout,
             "tracks": info.tracks, "items": info.items,
             "tuned": info.tuned, "best_ms": info.best_ms}
+
+
+def fit_relayout(src, src_layout: int, dst, dst_layout: int, n: Optional[int] = None,
+                 stream=None) -> None:
+    """Copies the (rows, ld) device array src into dst, converting between
+    FIT_LAYOUT_SOA and FIT_LAYOUT_AOSOA32 (4-byte elements; rows = all
+    leading dimensions of src but the last; n tracks, default all)."""
+    rows = int(np.prod(src.shape[:-1]))
+    n = src.shape[-1] if n is None else n
+    _check(load().fit_relayout(ctypes.c_void_p(src.data_ptr()), src.shape[-1], int(src_layout),
+                               ctypes.c_void_p(dst.data_ptr()), dst.shape[-1], int(dst_layout),
+                               rows, int(n), _stream_handle(stream)))
 
 
 def fit_plan_destroy(plan: int) -> None:

@@ -90,7 +90,7 @@ def test_header_compiles_as_c_and_matches_the_binding(tmp_path):
         pytest.skip("no C compiler")
     structs = {"fit_config": ["B", "nlayer", "surf", "max_iter", "tol", "start"],
                "fit_launch_config": ["threads_per_block", "blocks_per_sm", "persistent",
-                                     "tracks_per_thread"],
+                                     "tracks_per_thread", "layout"],
                "fit_plan_info": ["config", "tracks", "items", "tuned", "best_ms"],
                "fit_tracks_in": ["par", "cov", "q", "ld"],
                "fit_tracks_out": ["par", "cov", "q", "chi2", "chi2_layer", "status", "ld"],
@@ -121,8 +121,8 @@ def test_header_compiles_as_c_and_matches_the_binding(tmp_path):
 
 
 def test_plan_struct_layouts():
-    assert ctypes.sizeof(fit.fit_launch_config) == 16
-    assert fit.fit_plan_info.tracks.offset == 16
-    assert ctypes.sizeof(fit.fit_plan_info) == 40
+    assert ctypes.sizeof(fit.fit_launch_config) == 20
+    assert fit.fit_plan_info.tracks.offset == 24
+    assert ctypes.sizeof(fit.fit_plan_info) == 48
     assert ctypes.sizeof(fit.fit_candidates) == 32
     assert ctypes.sizeof(fit.fit_mlp_train_config) == 40

@@ -126,26 +126,103 @@ def test_plan_recaptures_for_a_new_hit_covariance_buffer():
         fit.fit_plan_destroy(plan)
         f.close()
 
-@pytest.mark.parametrize("tpb,bps,persistent,tpt", [(64, 1, 1, 2), (64, 6, 1, 2), (128, 1, 1, 2),
-                                                    (128, 3, 1, 2), (32, 12, 1, 2), (32, 1, 1, 2),
-                                                    (128, 0, 0, 2), (64, 0, 1, 1),
-                                                    (128, 2, 1, 1)])
-def test_every_launch_shape(tpb, bps, persistent, tpt):
+def _to_layout(dev_in, layout):
+    """The (SoA) track and hit arrays converted to `layout` with fit_relayout
+    (per-track arrays, q, are the same in both layouts)."""
+    if layout == fit.FIT_LAYOUT_SOA:
+        return dev_in
+    conv = []
+    for k, a in enumerate(dev_in):
+        if k == 2:
+            conv.append(a)
+            continue
+        b = torch.empty_like(a)
+        fit.fit_relayout(a, fit.FIT_LAYOUT_SOA, b, layout)
+        conv.append(b)
+    return conv
+
+
+def _from_layout(out, layout):
+    if layout == fit.FIT_LAYOUT_SOA:
+        return out
+    res = dict(out)
+    for k in ("par", "cov", "chi2_layer"):
+        if out.get(k) is not None:
+            b = torch.empty_like(out[k])
+            fit.fit_relayout(out[k], layout, b, fit.FIT_LAYOUT_SOA)
+            res[k] = b
+    return res
+
+
+@pytest.mark.parametrize("tpb,bps,persistent,tpt,layout",
+                         [(64, 1, 1, 2, 0), (64, 6, 1, 2, 0), (128, 1, 1, 2, 0), (128, 3, 1, 2, 0),
+                          (32, 12, 1, 2, 0), (32, 1, 1, 2, 0), (128, 0, 0, 2, 0), (64, 0, 1, 1, 0),
+                          (128, 2, 1, 1, 0), (256, 0, 1, 2, 0), (256, 1, 1, 1, 0),
+                          (256, 0, 1, 1, 0), (128, 0, 1, 2, 1), (32, 5, 1, 2, 1),
+                          (256, 0, 1, 2, 1), (64, 0, 1, 1, 1), (256, 2, 1, 1, 1),
+                          (128, 0, 0, 2, 1)])
+def test_every_launch_shape(tpb, bps, persistent, tpt, layout):
+    """Every axis the tuner searches (threads per block, blocks per SM,
+    persistent or per segment, tracks per thread, layout) against the oracle."""
     ev = _events(40, seed=41)
-    ld, dev_in = _device(ev)
+    ld, dev_in = _device(ev, ld=(ev.n + 31) // 32 * 32)
     f = fit.Fitter(*_geoms(ev))
     plan = fit.fit_plan_create(f.h, ev.ntrk, ev.mode, 20, threads_per_block=tpb,
                                blocks_per_sm=bps, persistent=bool(persistent),
-                               tracks_per_thread=tpt)
+                               tracks_per_thread=tpt, layout=layout)
     try:
         info = fit.fit_plan_get_info(plan)
         assert info["tracks_per_thread"] == tpt and info["threads_per_block"] == tpb
+        assert info["layout"] == layout
         out = _outputs(f, ev, ld)
-        fit.fit_plan_run(plan, *dev_in, par_out=out["par"], cov_out=out["cov"], q_out=out["q"],
-                         chi2=out["chi2"], status=out["status"])
+        fit.fit_plan_run(plan, *_to_layout(dev_in, layout), par_out=out["par"],
+                         cov_out=out["cov"], q_out=out["q"], chi2=out["chi2"],
+                         status=out["status"])
         st = f.sync()
         assert st["tracks"] == ev.n
-        _check_against_oracle(ev, _fetch(out, ev.n), f"shape {tpb},{bps},{persistent},{tpt}")
+        _check_against_oracle(ev, _fetch(_from_layout(out, layout), ev.n),
+                              f"shape {tpb},{bps},{persistent},{tpt},{layout}")
+    finally:
+        fit.fit_plan_destroy(plan)
+        f.close()
+
+
+def test_relayout_round_trip_and_errors():
+    a = torch.arange(7 * 96, dtype=torch.float32, device="cuda").reshape(7, 96)
+    b, c = torch.full_like(a, -1.0), torch.full_like(a, -1.0)
+    fit.fit_relayout(a, fit.FIT_LAYOUT_SOA, b, fit.FIT_LAYOUT_AOSOA32)
+    fit.fit_relayout(b, fit.FIT_LAYOUT_AOSOA32, c, fit.FIT_LAYOUT_SOA)
+    assert torch.equal(a, c)
+    # component k of track t sits at ((t / 32) * rows + k) * 32 + t % 32
+    t, k = 45, 3
+    assert b.reshape(-1)[((t // 32) * 7 + k) * 32 + t % 32].item() == a[k, t].item()
+    with pytest.raises(fit.FitError):  # AoSoA needs ld % 32 == 0
+        fit.fit_relayout(a[:, :90].contiguous(), fit.FIT_LAYOUT_SOA,
+                         torch.empty(7, 90, device="cuda"), fit.FIT_LAYOUT_AOSOA32)
+
+
+def test_tuner_chooses_the_layout():
+    """A plan created with FIT_LAYOUT_TUNE has every shape timed in both
+    layouts and then runs in the one chosen, which takes buffers in that
+    layout; the result matches the oracle."""
+    ev = _events(50, seed=53)
+    ld, dev_in = _device(ev, ld=(ev.n + 31) // 32 * 32)
+    f = fit.Fitter(*_geoms(ev))
+    plan = fit.fit_plan_create(f.h, ev.ntrk, ev.mode, 20, layout=fit.FIT_LAYOUT_TUNE)
+    try:
+        assert fit.fit_plan_get_info(plan)["layout"] == fit.FIT_LAYOUT_SOA  # until tuned
+        out = _outputs(f, ev, ld)
+        bufs = dict(par_out=out["par"], cov_out=out["cov"], q_out=out["q"], chi2=out["chi2"],
+                    status=out["status"])
+        info = fit.fit_plan_tune(plan, *dev_in, **bufs)
+        assert info["tuned"] == 1 and info["layout"] in (fit.FIT_LAYOUT_SOA, fit.FIT_LAYOUT_AOSOA32)
+        out = _outputs(f, ev, ld)
+        fit.fit_plan_run(plan, *_to_layout(dev_in, info["layout"]), par_out=out["par"],
+                         cov_out=out["cov"], q_out=out["q"], chi2=out["chi2"],
+                         status=out["status"])
+        f.sync()
+        _check_against_oracle(ev, _fetch(_from_layout(out, info["layout"]), ev.n),
+                              f"tuned layout {info['layout']}")
     finally:
         fit.fit_plan_destroy(plan)
         f.close()
@@ -169,7 +246,7 @@ def test_tune_and_cache(tmp_path):
         assert f.sync()["tracks"] == 0  # the tuning runs are not counted
         info2 = fit.fit_plan_tune(p2, *dev_in, cache_path=cache, **bufs)
         assert info2["tuned"] == 2
-        for k in ("threads_per_block", "blocks_per_sm", "persistent", "tracks_per_thread"):
+        for k in ("threads_per_block", "blocks_per_sm", "persistent", "tracks_per_thread", "layout"):
             assert info2[k] == info[k]
         fit.fit_plan_run(p2, *dev_in, **bufs)
         f.sync()
@@ -196,6 +273,8 @@ def test_plan_argument_errors():
             fit.fit_plan_create(f.h, [10], [0], 19)  # nlayer differs
         with pytest.raises(fit.FitError):
             fit.fit_plan_create(f.h, [10], [0], 20, threads_per_block=96)
+        with pytest.raises(fit.FitError):
+            fit.fit_plan_create(f.h, [10], [0], 20, layout=3)
         with pytest.raises(fit.FitError):  # one track per thread: 64 or 128 threads
             fit.fit_plan_create(f.h, [10], [0], 20, threads_per_block=32, tracks_per_thread=1)
         with pytest.raises(fit.FitError):  # ... and persistent only
