@@ -71,8 +71,14 @@ def set_nevt(n: int) -> None:
     NEVT = n
 
 
-def bytes_per_track_layer(nlayer: int) -> float:
-    return 36.0 + (BYTES_TRACK_IN + BYTES_TRACK_OUT) / nlayer
+# Hit bytes a track-layer needs: p2r measures the azimuthal coordinate and z
+# (all 3 positions and 6 covariance entries); p2z measures (x, y) on the
+# plane (2 positions, the 3 (x, y) covariance entries).
+HIT_BYTES = (36.0, 20.0)
+
+
+def bytes_per_track_layer(nlayer: int, mode: int = 0) -> float:
+    return HIT_BYTES[mode] + (BYTES_TRACK_IN + BYTES_TRACK_OUT) / nlayer
 
 
 def load_peaks() -> dict:
@@ -866,6 +872,68 @@ def bench_seed(args, world, rank, local):
     return line
 
 
+def bench_hostlink(args, world, rank, local):
+    """The host link under the end-to-end path: 1-D page-locked copies
+    (1.6 GB each way), and per mode the fused fit on host buffers through
+    the staged copies (fit_propagate_update_host) and in place over the link
+    (fit_propagate_update_mapped), against the same fit on device buffers."""
+    import torch
+    from paper_2409_09228_gb300 import fit
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def t_ms(fn, reps=5):
+        fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    nb = 1_600_000_000
+    h = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nb, dtype=torch.uint8, device=dev)
+    res = {"h2d_1d_GBs": nb / t_ms(lambda: d.copy_(h, non_blocking=True)) / 1e6,
+           "d2h_1d_GBs": nb / t_ms(lambda: h.copy_(d, non_blocking=True)) / 1e6}
+    del h, d
+    sets = workload(rank)
+    n = NEVT * NTRK
+    ntrk = [NTRK] * NEVT
+    f = fit.Fitter(fit.Geometry(sets[0].B, sets[0].surf), fit.Geometry(sets[1].B, sets[1].surf),
+                   device=local)
+    for m, name in ((0, "p2r"), (1, "p2z")):
+        s = sets[m]
+        arrs = (s.par0, s.cov0, s.q, s.hpos, s.hcov)
+        dd = [torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in arrs]
+        out_d = f.outputs(n, ld=n)
+        hin = [torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for v in arrs]
+        hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out_d.items()
+                if v is not None}
+        kw = dict(par_out=hout["par"], cov_out=hout["cov"], q_out=hout["q"], chi2=hout["chi2"],
+                  status=hout["status"], stream=stream)
+        nbytes = sum(t.numel() * t.element_size() for t in hin + list(hout.values()))
+        ms = {"device": t_ms(lambda: f.run(*dd, ntrk, [m] * NEVT, out=out_d, stream=stream)),
+              "staged": t_ms(lambda: fit.fit_propagate_update_host(f.h, *hin, ntrk, [m] * NEVT, **kw)),
+              "mapped": t_ms(lambda: fit.fit_propagate_update_mapped(f.h, *hin, ntrk, [m] * NEVT, **kw))}
+        res[name] = {"ms": ms, "host_bytes": nbytes,
+                     "mapped_GBs": nbytes / ms["mapped"] / 1e6, "staged_GBs": nbytes / ms["staged"] / 1e6}
+        f.sync(stream)
+    f.close()
+    if rank != 0:
+        return None
+    return {"metric": "host-link bandwidth and end-to-end time per mode", "value": res["p2z"]["mapped_GBs"],
+            "unit": "GB/s", "config": {"workload": f"{NEVT} events x {NTRK} tracks x {NLAYER} layers "
+                                                   f"per mode, page-locked host buffers"},
+            "hostlink": res}
+
+
 SECONDARY = {"uneven": bench_uneven, "adjoint": bench_adjoint, "seed": bench_seed,
              "f64": bench_f64, "layout": bench_layout, "find": bench_find}
 
@@ -917,7 +985,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--nevt", type=int, default=NEVT, help="events per mode (default 100)")
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "uneven", "adjoint", "seed", "f64", "layout", "find"],
+                    choices=["uniform", "uneven", "adjoint", "seed", "f64", "layout", "find",
+                             "hostlink"],
                     help="uniform: 100 x 9600 x 20 per mode (the default); uneven: the batched "
                          "form on 2000 events of log-normal size and mixed modes")
     ap.add_argument("--uneven-events", type=int, default=2000)
@@ -933,7 +1002,8 @@ def main():
         run_reference(args, world, rank)
         return
     if args.workload != "uniform":
-        line = SECONDARY[args.workload](args, world, rank, local)
+        fn = bench_hostlink if args.workload == "hostlink" else SECONDARY[args.workload]
+        line = fn(args, world, rank, local)
         if line is not None:
             print(json.dumps(line))
         return
@@ -1001,7 +1071,8 @@ def main():
     sms = sm_count(local)
     alu_peak = fp32_peak_tflops(peaks["sm_max_mhz"], sms)
     tl = n * NLAYER
-    bpl = bytes_per_track_layer(NLAYER)
+    bpls = [bytes_per_track_layer(NLAYER, m) for m in (0, 1)]
+    bpl = bpls[dom]
     alu_ach = flops[dom] * tl / (kernel_ms[dom] / 1e3) / 1e12
     hbm_ach = bpl * tl / (kernel_ms[dom] / 1e3) / 1e9
     t_alu = flops[dom] * tl / (alu_peak * 1e12)
@@ -1023,7 +1094,8 @@ def main():
                  "hbm_frac": hbm_ach / peaks["hbm_gbs"], "alu_frac": alu_ach / alu_peak,
                  "t_roof_us": {"alu": t_alu * 1e6, "hbm": t_hbm * 1e6, "mufu": t_mufu * 1e6},
                  "kernel_ms_p2r_p2z": kernel_ms,
-                 "frac_p2r_p2z": [max(flops[m] * tl / (alu_peak * 1e12), t_hbm) /
+                 "frac_p2r_p2z": [max(flops[m] * tl / (alu_peak * 1e12),
+                                      bpls[m] * tl / (peaks["hbm_gbs"] * 1e9)) /
                                   (kernel_ms[m] / 1e3) for m in (0, 1)],
                  "fp32_probe": fp32_probe})
 
