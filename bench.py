@@ -918,7 +918,11 @@ def bench_hostlink(args, world, rank, local):
                 if v is not None}
         kw = dict(par_out=hout["par"], cov_out=hout["cov"], q_out=hout["q"], chi2=hout["chi2"],
                   status=hout["status"], stream=stream)
-        nbytes = sum(t.numel() * t.element_size() for t in hin + list(hout.values()))
+        # bytes the fit moves over the link: track state in and out, and the hit
+        # components the update reads (p2z: x, y and their 3 covariance entries)
+        hit_frac = HIT_BYTES[m] / 36.0
+        nbytes = int(sum(t.numel() * t.element_size() for t in hin[:3] + list(hout.values())) +
+                     hit_frac * sum(t.numel() * t.element_size() for t in hin[3:]))
         ms = {"device": t_ms(lambda: f.run(*dd, ntrk, [m] * NEVT, out=out_d, stream=stream)),
               "staged": t_ms(lambda: fit.fit_propagate_update_host(f.h, *hin, ntrk, [m] * NEVT, **kw)),
               "mapped": t_ms(lambda: fit.fit_propagate_update_mapped(f.h, *hin, ntrk, [m] * NEVT, **kw))}
