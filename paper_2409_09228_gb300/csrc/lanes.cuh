@@ -42,10 +42,15 @@ __device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, 
 // Division and square root where a couple of ulp are far below the fit's
 // tolerance: the approximate reciprocal, square root and rsqrt (MUFU) instead
 // of the IEEE sequences.
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ F2 fdiv(F2 a, F2 b) {
-  return F2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y));
+__device__ __forceinline__ float frcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
+__device__ __forceinline__ F2 frcp(F2 x) { return F2(frcp(x.v.x), frcp(x.v.y)); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+// a * (1/b): the reciprocals per lane, the product packed
+__device__ __forceinline__ F2 fdiv(F2 a, F2 b) { return a * frcp(b); }
 // Approximate square root (one MUFU operation, relative error ~2^-23); NaN
 // for x < 0, which every caller either excludes by its own test or sends
 // down a failing branch.
@@ -93,7 +98,8 @@ __device__ __forceinline__ F2 sel(M2 m, F2 a, F2 b) {
 // ---- double (the FP64 variant, one track per thread): IEEE operations ------
 __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
-__device__ __forceinline__ double fsqrt(double x) { return x > 0.0 ? ::sqrt(x) : 0.0; }
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double fsqrt(double x) { return ::sqrt(x); }  // NaN for x < 0, as in FP32
 __device__ __forceinline__ double frsqrt(double x) { return 1.0 / ::sqrt(x); }
 __device__ __forceinline__ double fabs_(double x) { return ::fabs(x); }
 __device__ __forceinline__ double floor_(double x) { return ::floor(x); }

@@ -158,10 +158,12 @@ __device__ __forceinline__ void sinc_cs(float u, float& s, float& cu, float& sp)
 }
 __device__ __forceinline__ void sinc_cs(F2 u, F2& s, F2& cu, F2& sp) {
   const F2 au = fabs_(u);
-  if (all(le(au, F2(1.25f)))) {
-    const bool shortform = all(le(au, F2(0.1f)));
-    sinc_series(u * u, s, cu, shortform);
-    sp = sinc_deriv_series(u, shortform);
+  if (all(le(au, F2(0.1f)))) {  // the common case first: one test
+    sinc_series(u * u, s, cu, true);
+    sp = sinc_deriv_series(u, true);
+  } else if (all(le(au, F2(1.25f)))) {
+    sinc_series(u * u, s, cu, false);
+    sp = sinc_deriv_series(u, false);
   } else {
     sinc_cs(u.v.x, s.v.x, cu.v.x, sp.v.x);
     sinc_cs(u.v.y, s.v.y, cu.v.y, sp.v.y);
@@ -180,17 +182,22 @@ __device__ __forceinline__ void turn(T& c, T& s, T cd, T sd) {
 // As turn(), for an angle d given by value: the change of an angle in one
 // update is small, so the Taylor series of sin d and cos d (to d^5 and d^4,
 // remainders < 2e-9 for |d| <= 0.1) replace a trigonometric call.
+// turn_small: the series alone, for a caller that knows |d| <= 0.1.
+template <class T>
+__device__ __forceinline__ void turn_small(T& c, T& s, T d) {
+  const T d2 = d * d;
+  turn(c, s, fma(d2, fma(d2, T(4.1666667e-02f), T(-0.5f)), T(1.0f)),
+       d * fma(d2, fma(d2, T(8.3333333e-03f), T(-1.6666667e-01f)), T(1.0f)));
+}
 template <class T>
 __device__ __forceinline__ void turn_by(T& c, T& s, T d) {
-  T sd, cd;
   if (all(le(fabs_(d), T(0.1f)))) {
-    const T d2 = d * d;
-    sd = d * fma(d2, fma(d2, T(8.3333333e-03f), T(-1.6666667e-01f)), T(1.0f));
-    cd = fma(d2, fma(d2, T(4.1666667e-02f), T(-0.5f)), T(1.0f));
+    turn_small(c, s, d);
   } else {
+    T sd, cd;
     sincos_cw(d, sd, cd);
+    turn(c, s, cd, sd);
   }
-  turn(c, s, cd, sd);
 }
 
 // FP64 variant: sin and cos from the CUDA math library; sin(u)/u and its
@@ -221,6 +228,7 @@ __device__ __forceinline__ void turn_by(double& c, double& s, double d) {
   ::sincos(d, &sd, &cd);
   turn(c, s, cd, sd);
 }
+__device__ __forceinline__ void turn_small(double& c, double& s, double d) { turn_by(c, s, d); }
 __device__ __forceinline__ void sinc_cs(double u, double& s, double& cu, double& sp) {
   sinc_c(u, s, cu);
   sp = sinc_deriv(u, s, cu);
@@ -230,11 +238,8 @@ __device__ __forceinline__ void sinc_cs(double u, double& s, double& cu, double&
 template <class T>
 __device__ __forceinline__ void turn_by2(T& c1, T& s1, T d1, T& c2, T& s2, T d2) {
   if (all(le(fmax_(fabs_(d1), fabs_(d2)), T(0.1f)))) {
-    const T q1 = d1 * d1, q2 = d2 * d2;
-    turn(c1, s1, fma(q1, fma(q1, T(4.1666667e-02f), T(-0.5f)), T(1.0f)),
-         d1 * fma(q1, fma(q1, T(8.3333333e-03f), T(-1.6666667e-01f)), T(1.0f)));
-    turn(c2, s2, fma(q2, fma(q2, T(4.1666667e-02f), T(-0.5f)), T(1.0f)),
-         d2 * fma(q2, fma(q2, T(8.3333333e-03f), T(-1.6666667e-01f)), T(1.0f)));
+    turn_small(c1, s1, d1);
+    turn_small(c2, s2, d2);
   } else {
     turn_by(c1, s1, d1);
     turn_by(c2, s2, d2);
@@ -547,8 +552,8 @@ __device__ __forceinline__ typename Lanes<T>::M crossing_start(T x, T y, T cph, 
   const T den = b0 + fsqrt(X);
   const T hl = fdiv(-c0, den);
   const T t = T(0.5f) * kappa * hl;
-  const M ok = and_(and_(le(c0, T(0.f)), le(T(0.f), X)),
-                    and_(lt(T(0.f), den), le(fabs_(t), T(0.25f))));
+  // X < 0 (the circle misses the cylinder) makes den NaN, which fails den > 0
+  const M ok = and_(le(c0, T(0.f)), and_(lt(T(0.f), den), le(fabs_(t), T(0.25f))));
   h = hl * atan_ratio(t);
   if constexpr (Lanes<T>::n > 1 || !EXACT) {
     return not_(ok);
@@ -604,6 +609,7 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
   const T sph = g.sphi, cph = g.cphi;
   const T x = p[0], y = p[1];
   const T R2 = T(R) * T(R);
+  const T hk = T(0.5f) * kappa;  // u = hk h
   const T b0 = fma(x, cph, y * sph);
   const T c0 = fma(x, x, fma(y, y, -R2));
   const M inside = le(c0, T(0.f));
@@ -618,7 +624,7 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
     // R only if |c| + rho >= R, which always holds when rho >= R.
     fail = lt(T(1.f), T(R) * fabs_(kappa));
     if (any(fail)) {
-      const T irs = fdiv(T(1.f), kappa);  // signed radius
+      const T irs = frcp(kappa);  // signed radius
       const T cx = fma(-sph, irs, x), cy = fma(cph, irs, y);
       fail = and_(fail, lt(fsqrt(fma(cx, cx, cy * cy)) + fabs_(irs), T(R)));
     }
@@ -647,7 +653,7 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
   auto step = [&]() {
 #pragma unroll
     for (int i = 0; i < Lanes<T>::n; ++i) iters[i] += Lanes<T>::get(conv, i) ? 0u : 1u;
-    u = T(0.5f) * kappa * h;
+    u = hk * h;
     sinc_cs(u, s, cu, sp);
     const T su = u * s;
     cm = cph;
@@ -699,14 +705,14 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
   // once |d| <= tol) and turn the direction by kappa d.
   px = fma(d, c1, px);
   py = fma(d, s1, py);
-  const T isth = fdiv(T(1.f), g.sth);
+  const T isth = frcp(g.sth);
   const T cot = g.cth * isth;
   const T dx = px - x, dy = py - y;
   const T hh = T(0.5f) * h * h * dkdw;
   const T Xw = hh * fma(sp, cm, -(s * sm));
   const T Yw = hh * fma(sp, sm, s * cm);
   // grad h = -grad g / (dg/dh) with g = x'^2 + y'^2 - R^2.
-  const T iD = fdiv(T(1.f), fma(px, c1, py * s1));
+  const T iD = frcp(fma(px, c1, py * s1));
   const T hx = -(px * iD), hy = -(py * iD);
   const T hw = -(fma(px, Xw, py * Yw) * iD);
   const T hp = fma(px, dy, -(py * dx)) * iD;
@@ -720,7 +726,12 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
   p[1] = py;
   p[2] = fma(h, cot, p[2]);
   p[4] = fma(kappa, h, p[4]);
-  turn_by(c1, s1, kappa * d);
+  // the last step d is below the tolerance on converged lanes, so kappa d
+  // is far inside the series' range and needs no range test
+  if (!any(notconv))
+    turn_small(c1, s1, kappa * d);
+  else
+    turn_by(c1, s1, kappa * d);
   g.cphi = c1;
   g.sphi = s1;
   return fail;
