@@ -239,6 +239,29 @@ def test_crossing_start_reach_and_roots_on_random_states():
           f"reach decisions differ; {it[fair].mean():.4f} iterations on {fair.sum()}")
 
 
+def test_not_converged_tracks_are_flagged_and_counted():
+    """The iteration's limit: from the straight-line start with max_iter = 1 most
+    p2r track-layers stop one step short of the tolerance.  Those tracks carry
+    the NOT_CONVERGED bit, the counter equals the flags, their outputs stay
+    finite (the last iterate, with its direction turned by the general
+    rotation rather than the converged-step series), and with enough
+    iterations the same tracks match the oracle."""
+    ts = inputs.generate(inputs.MODE_R, 3000, seed=77)
+    g1 = gpu_util.run([ts], max_iter=1, start=fit.FIT_START_LINE)
+    st = g1["status"][:ts.n]
+    flagged = (st & fit.FIT_ST_NOT_CONVERGED) != 0
+    assert flagged.sum() > ts.n // 2
+    assert g1["sync"]["not_converged"] == int(flagged.sum())
+    assert ((st & ~np.uint8(fit.FIT_ST_NOT_CONVERGED)) == 0).all()
+    for k in ("par", "cov", "chi2"):
+        assert np.isfinite(g1[k][..., :ts.n]).all(), k
+    # one step short of the root moves the state by less than the step itself
+    g10 = gpu_util.run([ts], max_iter=10, start=fit.FIT_START_LINE)
+    assert (g10["status"][:ts.n] == 0).all()
+    assert np.abs(g1["par"][:3, :ts.n] - g10["par"][:3, :ts.n]).max() < 0.05
+    parity.check(gpu_util.trim(g10, 0, ts.n), oracle.fit_set(ts), "max_iter 10, line start")
+
+
 def test_bad_start_is_an_argument_error():
     with pytest.raises(fit.FitError) as e:
         fit.Fitter(fit.Geometry(3.8, inputs.surfaces(0), start=7), None)
