@@ -65,10 +65,11 @@ __global__ void __launch_bounds__(BLK, batched_min_blocks(BLK, TPT))
       if (t < w.end) {
         unsigned st = 0u, iters = 0u;
         State<float> s;
-        load_state<L>(b.a, t, s);
         if (w.mode == FIT_MODE_Z) {
+          begin_state<FIT_MODE_Z, L>(b.a, b.geo[FIT_MODE_Z], t, s);
           finish_one<FIT_MODE_Z, L>(b.a, b.geo[FIT_MODE_Z], t, 0, s, st, iters, true);
         } else {
+          begin_state<FIT_MODE_R, L>(b.a, b.geo[FIT_MODE_R], t, s);
           finish_one<FIT_MODE_R, L>(b.a, b.geo[FIT_MODE_R], t, 0, s, st, iters, true);
           count_iterations(iters, &b.a.counters[4]);
         }

@@ -50,7 +50,10 @@ template <int MODE, class T>
 __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant__ FindArgs<T> a) {
   const int64_t t = a.t0 + (int64_t)blockIdx.x * kBlock + threadIdx.x;
   if (t >= a.t1) return;
-  T p[6], c[21];
+  // The covariance in the fused fit's loop form (fused.cuh, enter_loop_form):
+  // p2z c with a zero z row, p2r the local form cl with the null direction
+  // (bc, bs).
+  T p[6], c[21], cl[15], bc, bs;
 #pragma unroll
   for (int k = 0; k < 6; ++k) fitk::ld(p[k], a.par_in + k * a.ld_in + t);
 #pragma unroll
@@ -58,6 +61,16 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
   T qf = (T)__ldcs(a.q_in + t);
   T chi2 = T(0.f);
   fitk::Trig<T> g = fitk::trig_of(p);
+  {
+    const T kappa = qf * -a.kB * p[3];
+    if (MODE == FIT_MODE_Z) {
+      fitk::enter_plane(c, g, kappa);
+    } else {
+      fitk::enter_line(c, g, kappa, cl);
+      bc = g.cphi;
+      bs = g.sphi;
+    }
+  }
   unsigned st = 0u, iters[1] = {0u};
   const Geo& geo = a.geo;
   const int64_t ldc = a.ld_cand;
@@ -77,11 +90,11 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
       if (propagated)
         propagated = false;
       else if (MODE == FIT_MODE_Z)
-        failed = fitk::prop_z(p, c, g, dkdw, sf);
+        failed = fitk::prop_z<true>(p, c, g, dkdw, sf);
       else
-        failed = fitk::prop_r<T, false, fitk::Start::kFast>(p, c, g, dkdw, sf, geo.max_iter,
-                                                             geo.tol * sf, geo.line_start, iters,
-                                                             nc);
+        failed = fitk::prop_r_local<T, fitk::Start::kFast>(p, cl, bc, bs, g, dkdw, sf,
+                                                           geo.max_iter, geo.tol * sf,
+                                                           geo.line_start, iters, nc);
       if (failed) {
         if (MODE == FIT_MODE_R && !geo.line_start)
           rerun = true;
@@ -100,7 +113,8 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
         for (int j = 0; j < 3; ++j) fitk::ld(m[j], cp + (3 * k + j) * ldc);
 #pragma unroll
         for (int j = 0; j < 6; ++j) fitk::ld(v[j], cc + (6 * k + j) * ldc);
-        const T x = (MODE == FIT_MODE_Z) ? fitk::chi2_z(p, c, m, v) : fitk::chi2_r(p, c, m, v);
+        const T x = (MODE == FIT_MODE_Z) ? fitk::chi2_z(p, c, m, v)
+                                         : fitk::chi2_r_local(p, cl, bc, bs, m, v);
         if (x < best_chi2) {
           best = k;
           best_chi2 = x;
@@ -115,8 +129,15 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
 #pragma unroll
         for (int j = 0; j < 6; ++j) fitk::ld(v[j], cc + (6 * best + j) * ldc);
         const T phi_pred = p[4], th_pred = p[5];
-        x2 = (MODE == FIT_MODE_Z) ? fitk::update_z(p, c, m, v) : fitk::update_r(p, c, m, v);
-        if (fitk::normalise(p, c, qf, g, phi_pred, th_pred)) st |= FIT_ST_CHARGE_FLIP;
+        bool flip;
+        if (MODE == FIT_MODE_Z) {
+          x2 = fitk::update_z<true>(p, c, m, v);
+          flip = fitk::normalise(p, c, qf, g, phi_pred, th_pred);
+        } else {
+          x2 = fitk::update_r_local(p, cl, bc, bs, m, v);
+          flip = fitk::normalise(p, cl, qf, g, phi_pred, th_pred);
+        }
+        if (flip) st |= FIT_ST_CHARGE_FLIP;
         if (!fitk::finite_(x2)) {
           st |= FIT_ST_NONFINITE;
           x2 = T(0.f);
@@ -133,8 +154,8 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
     const T dkdw = qf * -a.kB;
     const T h0 = fitk::crossing_exact<T>(p[0], p[1], g.cphi, g.sphi, dkdw * p[3], T(sf));
     bool nc = false;
-    if (fitk::prop_r<T, false, fitk::Start::kGiven>(p, c, g, dkdw, sf, geo.max_iter,
-                                                    geo.tol * sf, false, iters, nc, T(0.f), h0)) {
+    if (fitk::prop_r_local<T, fitk::Start::kGiven>(p, cl, bc, bs, g, dkdw, sf, geo.max_iter,
+                                                   geo.tol * sf, false, iters, nc, h0)) {
       st |= FIT_ST_NO_INTERSECTION;
       break;
     }
@@ -144,6 +165,12 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
   for (int r = l; r < a.nlayer; ++r) {  // layers not reached
     a.chosen[(int64_t)r * a.ld_out + t] = -1;
     if (a.chi2_layer) a.chi2_layer[(int64_t)r * a.ld_out + t] = T(0.f);
+  }
+  if (l == 0) {  // nothing applied: the input covariance
+#pragma unroll
+    for (int k = 0; k < 21; ++k) fitk::ld(c[k], a.cov_in + k * a.ld_in + t);
+  } else if (MODE == FIT_MODE_R) {
+    fitk::to_global_r(cl, bc, bs, c);
   }
   bool fin = fitk::finite_(chi2);
 #pragma unroll

@@ -26,9 +26,14 @@ using fitk::F2;
 using fitk::Lanes;
 
 // One or two tracks (lane type T) in registers for the whole layer loop.
+// The layer loop carries the covariance in a loop form (enter_loop_form):
+// for p2r the cylinder's local form cl with the null direction (bc, bs)
+// (fitk::to_local_r), for p2z c with a zero z row.  c holds the 6x6
+// covariance at load and store.
 template <class T>
 struct State {
   T p[6], c[21];
+  T cl[15], bc, bs;
   T qf;    // charge as +-1.f
   T chi2;  // sum over layers
   fitk::Trig<T> g;
@@ -66,13 +71,41 @@ __device__ __forceinline__ void load_state(const FitArgs& a, int64_t t, State<F2
   s.g = fitk::trig_of(s.p);
 }
 
-// Lane i of a two-track state as a one-track state.
+// The covariance of s in the loop form, projected onto a surface through the
+// start point (fitk::enter_plane, fitk::enter_line): every layer, the first
+// included, then propagates from the loop form, and the fit's results are
+// those of the 6x6 form.  leave_loop_form: back to the 6x6 covariance in c.
+template <int MODE, class T>
+__device__ __forceinline__ void enter_loop_form(State<T>& s, float kB) {
+  const T kappa = s.qf * T(-kB) * s.p[3];
+  if (MODE == FIT_MODE_Z) {
+    fitk::enter_plane(s.c, s.g, kappa);
+  } else {
+    fitk::enter_line(s.c, s.g, kappa, s.cl);
+    s.bc = s.g.cphi;
+    s.bs = s.g.sphi;
+  }
+}
+template <int MODE, class T>
+__device__ __forceinline__ void leave_loop_form(State<T>& s) {
+  if (MODE == FIT_MODE_R) fitk::to_global_r(s.cl, s.bc, s.bs, s.c);
+}
+
+// Lane i of a two-track state (in the loop form) as a one-track state.
+template <int MODE>
 __device__ __forceinline__ State<float> lane_of(const State<F2>& s, int i) {
   State<float> r;
 #pragma unroll
   for (int k = 0; k < 6; ++k) r.p[k] = Lanes<F2>::get(s.p[k], i);
+  if (MODE == FIT_MODE_Z) {
 #pragma unroll
-  for (int k = 0; k < 21; ++k) r.c[k] = Lanes<F2>::get(s.c[k], i);
+    for (int k = 0; k < 21; ++k) r.c[k] = Lanes<F2>::get(s.c[k], i);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 15; ++k) r.cl[k] = Lanes<F2>::get(s.cl[k], i);
+    r.bc = Lanes<F2>::get(s.bc, i);
+    r.bs = Lanes<F2>::get(s.bs, i);
+  }
   r.qf = Lanes<F2>::get(s.qf, i);
   r.chi2 = Lanes<F2>::get(s.chi2, i);
   r.g = {Lanes<F2>::get(s.g.cphi, i), Lanes<F2>::get(s.g.sphi, i), Lanes<F2>::get(s.g.cth, i),
@@ -106,8 +139,8 @@ __device__ __forceinline__ void store_state(const FitArgs& a, int64_t t, const S
 }
 
 // The fused layer loop (paper Sec. 3.1: propagate to the next layer, update
-// with its hit) for the lanes of s, tracks t, t+1, ..., from layer l0.
-// MODE selects the surface type at compile time.  Returns the layer whose
+// with its hit) for the lanes of s (in the loop form), tracks t, t+1, ...,
+// from layer l0.  MODE selects the surface type at compile time.  Returns the layer whose
 // surface some live lane cannot reach (its propagation is not applied), the
 // layer after one where a packed lane turned non-finite, or nlayer.  A lane
 // whose update turns non-finite stops (alive false); its later per-layer
@@ -146,14 +179,21 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
     const T dkdw = s.qf * T(-geo.kB);
     M fail, nc = fitk::lt(T(1.f), T(0.f));
     if (MODE == FIT_MODE_Z)
-      fail = fitk::prop_z(s.p, s.c, s.g, dkdw, sf);
+      fail = fitk::prop_z<true>(s.p, s.c, s.g, dkdw, sf);
     else
-      fail = fitk::prop_r(s.p, s.c, s.g, dkdw, sf, geo.max_iter, geo.tol * sf,
-                          geo.line_start, iters, nc);
+      fail = fitk::prop_r_local(s.p, s.cl, s.bc, s.bs, s.g, dkdw, sf, geo.max_iter,
+                                geo.tol * sf, geo.line_start, iters, nc);
     if (fitk::any(fitk::and_(fail, alive))) return done(l);
     const T phi_pred = s.p[4], th_pred = s.p[5];
-    T x2 = (MODE == FIT_MODE_Z) ? fitk::update_z(s.p, s.c, m, v) : fitk::update_r(s.p, s.c, m, v);
-    const M flip = fitk::normalise(s.p, s.c, s.qf, s.g, phi_pred, th_pred);
+    T x2;
+    M flip;
+    if (MODE == FIT_MODE_Z) {
+      x2 = fitk::update_z<true>(s.p, s.c, m, v);
+      flip = fitk::normalise(s.p, s.c, s.qf, s.g, phi_pred, th_pred);
+    } else {
+      x2 = fitk::update_r_local(s.p, s.cl, s.bc, s.bs, m, v);
+      flip = fitk::normalise(s.p, s.cl, s.qf, s.g, phi_pred, th_pred);
+    }
     alive = fitk::and_(alive, fitk::finite_(x2));
     any_nc = fitk::or_(any_nc, nc);
     any_flip = fitk::or_(any_flip, flip);
@@ -177,15 +217,38 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
   return done(a.nlayer);
 }
 
+// Outputs of a state that run_layers left at layer l: the loop form back to
+// the 6x6 covariance, or, where nothing was applied (l = 0: no layers, or
+// the first surface out of reach), the input covariance again -- read from
+// memory, so that no lane keeps it in registers through the loop.
+template <int MODE, int L, class T>
+__device__ __forceinline__ void finish_state(const FitArgs& a, int64_t t, int l, State<T>& s) {
+  if (l > 0) {
+    leave_loop_form<MODE>(s);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 21; ++k) fitk::ld(s.c[k], a.cov_in + ix<L>(k, t, a.ld_in, 21));
+  }
+}
+
+// A new track (or pair) from memory, in the loop form.
+template <int MODE, int L, class T>
+__device__ __forceinline__ void begin_state(const FitArgs& a, const Geo& geo, int64_t t,
+                                            State<T>& s) {
+  load_state<L>(a, t, s);
+  enter_loop_form<MODE>(s, geo.kB);
+}
+
 // One track alone from layer l0 to the end (or to a surface it cannot
-// reach), then its outputs.
+// reach), then its outputs; s is in the loop form.
 template <int MODE, int L = 0>
 __device__ __forceinline__ void finish_one(const FitArgs& a, const Geo& geo, int64_t t, int l0,
                                            State<float>& s, unsigned& st, unsigned& iters,
                                            bool alive) {
   unsigned st1[1] = {st}, it1[1] = {iters};
+  int l = l0;
   if (alive) {
-    const int l = run_layers<MODE, float, L>(a, geo, t, l0, s, st1, it1, alive);
+    l = run_layers<MODE, float, L>(a, geo, t, l0, s, st1, it1, alive);
     if (l < a.nlayer) {
       st1[0] |= FIT_ST_NO_INTERSECTION;
       if (a.chi2_layer)
@@ -194,6 +257,7 @@ __device__ __forceinline__ void finish_one(const FitArgs& a, const Geo& geo, int
   } else if (a.chi2_layer) {  // stopped earlier: no later layer adds to chi2
     for (int r = l0; r < a.nlayer; ++r) a.chi2_layer[ix<L>(r, t, a.ld_out, a.nlayer)] = 0.f;
   }
+  finish_state<MODE, L>(a, t, l, s);
   store_state<L>(a, t, s, st1);
   st = st1[0];
   iters = it1[0];
@@ -210,22 +274,23 @@ __device__ __forceinline__ void run_pair(const FitArgs& a, const Geo& geo, int64
   const bool v0 = t >= t0, v1 = t + 1 < t1;
   if (v0 && v1) {
     State<F2> s;
-    load_state<L>(a, t, s);
+    begin_state<MODE, L>(a, geo, t, s);
     fitk::M2 alive = {true, true};
     const int l = run_layers<MODE, F2, L>(a, geo, t, 0, s, st, iters, alive);
     if (l == a.nlayer) {
+      finish_state<MODE, L>(a, t, l, s);
       store_state<L>(a, t, s, st);
       return;
     }
 #pragma unroll 1
     for (int i = 0; i < 2; ++i) {
-      State<float> one = lane_of(s, i);
+      State<float> one = lane_of<MODE>(s, i);
       finish_one<MODE, L>(a, geo, t + i, l, one, st[i], iters[i], Lanes<F2>::get(alive, i));
     }
   } else {
     const int i = v0 ? 0 : 1;
     State<float> one;
-    load_state<L>(a, t + i, one);
+    begin_state<MODE, L>(a, geo, t + i, one);
     finish_one<MODE, L>(a, geo, t + i, 0, one, st[i], iters[i], true);
   }
 }

@@ -434,9 +434,185 @@ __device__ __forceinline__ void similarity_rank1(T (&c)[21], T f03, T f04, T f13
     }
 }
 
-// Propagation to the plane z = Z.  Returns the mask of lanes whose plane is
-// behind them; if any lane fails nothing is modified.
+// p2r covariance in the cylinder's local coordinates.  A propagated
+// covariance C' = J C J^T has the surface normal as a null vector: the
+// constraint x'^2 + y'^2 = R^2 gives x' J_x + y' J_y = 0 for the position
+// rows of J, and the Kalman update C - C H^T S^-1 H C keeps every null vector
+// of C.  So from the first cylinder on, C = B c B^T exactly, with c the 5x5
+// covariance of (l, z, w, phi, theta), l the position along the direction
+// (-bs, bc) normal to the null vector (bc, bs), and B the 6x5 basis
+// (-bs, bc) e_l + e_z ... e_theta.  The transport to the next cylinder is
+// then c' = J_l c J_l^T with the 5x5 J_l = P' J B (P' = B'^T, the projection
+// at the new point, whose null vector is its azimuth), and the update acts on
+// c with the projected measurement: the same results as the 6x6 form in
+// exact arithmetic, on 15 entries instead of 21.  to_local_r / to_global_r
+// move between the two forms.
 template <class T>
+__device__ __forceinline__ void to_local_r(const T (&c)[21], T bc, T bs, T (&cl)[15]) {
+  // l = -bs x + bc y
+  cl[sym(0, 0)] = fma(bs * bs, c[sym(0, 0)],
+                      fma(bc * bc, c[sym(1, 1)], T(-2.f) * (bs * bc) * c[sym(1, 0)]));
+#pragma unroll
+  for (int i = 1; i < 5; ++i) {
+    cl[sym(i, 0)] = fma(bc, c[sym(i + 1, 1)], -(bs * c[sym(i + 1, 0)]));
+#pragma unroll
+    for (int j = 1; j <= i; ++j) cl[sym(i, j)] = c[sym(i + 1, j + 1)];
+  }
+}
+template <class T>
+__device__ __forceinline__ void to_global_r(const T (&cl)[15], T bc, T bs, T (&c)[21]) {
+  const T l0 = cl[sym(0, 0)];
+  c[sym(0, 0)] = (bs * bs) * l0;
+  c[sym(1, 0)] = -(bs * bc) * l0;
+  c[sym(1, 1)] = (bc * bc) * l0;
+#pragma unroll
+  for (int i = 1; i < 5; ++i) {
+    c[sym(i + 1, 0)] = -(bs * cl[sym(i, 0)]);
+    c[sym(i + 1, 1)] = bc * cl[sym(i, 0)];
+#pragma unroll
+    for (int j = 1; j <= i; ++j) c[sym(i + 1, j + 1)] = cl[sym(i, j)];
+  }
+}
+
+// The start covariance in the loop form, for any start point.  The first
+// propagation's J C J^T is unchanged if C is first carried to a surface
+// through the start point itself: the map to the first surface passes that
+// surface at path length 0, so by the chain rule J = J J_0 with J_0 the
+// Jacobian of the zero-length propagation there, J_0 = I + v g^T
+// (v = d p / d h = (cos phi, sin phi, cot theta, 0, kappa, 0), g = grad h).
+// With y = C g and sigma = g^T y, J_0 C J_0^T = C + n v^T + v n^T,
+// n = y + (sigma / 2) v.
+//
+// p2z: the plane z = z0, g = -tan(theta) e_z; the z row of J_0 vanishes
+// (1 - cot tan = 0), which leaves the zero z row prop_z<true> needs.
+template <class T>
+__device__ __forceinline__ void enter_plane(T (&c)[21], const Trig<T>& g, T kappa) {
+  const T tn = fdiv(g.sth, g.cth);
+  const T sig = (tn * tn) * c[sym(2, 2)];
+  const T v[6] = {g.cphi, g.sphi, T(0.f), T(0.f), kappa, T(0.f)};
+  constexpr unsigned VM = (1u << 0) | (1u << 1) | (1u << 4);
+  T n[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    n[i] = (VM & (1u << i)) ? fma(T(0.5f) * sig, v[i], -(tn * c[sym(i, 2)])) : -(tn * c[sym(i, 2)]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      if (i == 2 || j == 2) {
+        c[sym(i, j)] = T(0.f);
+        continue;
+      }
+      T acc = c[sym(i, j)];
+      if (VM & (1u << j)) acc = fma(n[i], v[j], acc);
+      if (VM & (1u << i)) acc = fma(v[i], n[j], acc);
+      c[sym(i, j)] = acc;
+    }
+}
+
+// p2r: the line through the start point across the transverse direction,
+// (x - x0) cos phi + (y - y0) sin phi = 0, where g = -(cos phi, sin phi, 0,
+// 0, 0, 0) (well conditioned for any start, unlike the cylinder through it).
+// Its normal (cos phi, sin phi) is the null vector of the result, whose local
+// form (to_local_r) is returned with (bc, bs) = (cos phi, sin phi):
+// cl = B^T C B + n_l v_l^T + v_l n_l^T with v_l = B^T v = (0, cot, 0, kappa,
+// 0) and n_l = B^T y + (sigma / 2) v_l.
+template <class T>
+__device__ __forceinline__ void enter_line(const T (&c)[21], const Trig<T>& g, T kappa,
+                                           T (&cl)[15]) {
+  const T bc = g.cphi, bs = g.sphi;
+  const T cot = fdiv(g.cth, g.sth);
+  T y[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) y[i] = -fma(bc, c[sym(i, 0)], bs * c[sym(i, 1)]);
+  const T sig = -fma(bc, y[0], bs * y[1]);
+  to_local_r(c, bc, bs, cl);
+  const T hs = T(0.5f) * sig;
+  const T n[5] = {fma(bc, y[1], -(bs * y[0])), fma(hs, cot, y[2]), y[3], fma(hs, kappa, y[4]),
+                  y[5]};
+  const T v[5] = {T(0.f), cot, T(0.f), kappa, T(0.f)};
+  constexpr unsigned VM = (1u << 1) | (1u << 3);
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      T acc = cl[sym(i, j)];
+      if (VM & (1u << j)) acc = fma(n[i], v[j], acc);
+      if (VM & (1u << i)) acc = fma(v[i], n[j], acc);
+      cl[sym(i, j)] = acc;
+    }
+}
+
+// c <- J_l c J_l^T in local coordinates.  With J = A + v g^T as for
+// similarity_rank1, J_l = A_l + v_l g_l^T where g_l = B^T g = (gl0, 0, hw,
+// hp, 0), v_l = P' v = (vl0, cot, 0, kappa, 0) and A_l = P' A B differs from
+// the identity in the entries (l, l) = ctt (the cosine of the angle between
+// the two l directions), (l, w) = a02, (l, phi) = a03, (z, theta) = f25 and
+// (phi, w) = g43.  A_l = (I + G)(D + F) with D = diag(ctt, 1, ...), F the l
+// and z rows (reading only rows w, phi, theta) and G the phi row, so both
+// factors apply in place; then the rank-2 update as in similarity_rank1.
+template <class T>
+__device__ __forceinline__ void similarity_local_r(T (&c)[15], T ctt, T a02, T a03, T f25, T g43,
+                                                   T gl0, T hw, T hp, T vl0, T cot, T kappa) {
+  // m = c g_l, s = g_l^T m
+  T m[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    m[i] = fma(c[sym(i, 3)], hp, fma(c[sym(i, 2)], hw, c[sym(i, 0)] * gl0));
+  const T sg = fma(hp, m[3], fma(hw, m[2], gl0 * m[0]));
+  // D + F.  Row z: R1 = e_z + f25 e_theta; row l: R0 = ctt e_l + a02 e_w + a03 e_phi.
+  // X_il = (R_i c)_l for l in w, phi, theta are the new cross blocks.
+  T X1[3], X0[3];
+#pragma unroll
+  for (int l = 2; l < 5; ++l) X1[l - 2] = fma(f25, c[sym(4, l)], c[sym(1, l)]);
+  const T c11 = fma(f25, X1[2], fma(f25, c[sym(4, 1)], c[sym(1, 1)]));
+  const T c10 = fma(a03, X1[1], fma(a02, X1[0], ctt * fma(f25, c[sym(4, 0)], c[sym(1, 0)])));
+  const T y0 = fma(a03, c[sym(3, 0)], fma(a02, c[sym(2, 0)], ctt * c[sym(0, 0)]));
+#pragma unroll
+  for (int l = 2; l < 5; ++l)
+    X0[l - 2] = fma(a03, c[sym(3, l)], fma(a02, c[sym(2, l)], ctt * c[sym(0, l)]));
+  c[sym(0, 0)] = fma(a03, X0[1], fma(a02, X0[0], ctt * y0));
+  c[sym(1, 0)] = c10;
+  c[sym(1, 1)] = c11;
+#pragma unroll
+  for (int l = 2; l < 5; ++l) {
+    c[sym(1, l)] = X1[l - 2];
+    c[sym(0, l)] = X0[l - 2];
+  }
+  // G: row phi += g43 row w (and column phi likewise)
+  {
+    const T c32 = c[sym(3, 2)];
+    c[sym(3, 0)] = fma(g43, c[sym(2, 0)], c[sym(3, 0)]);
+    c[sym(3, 1)] = fma(g43, c[sym(2, 1)], c[sym(3, 1)]);
+    c[sym(4, 3)] = fma(g43, c[sym(4, 2)], c[sym(4, 3)]);
+    const T c32n = fma(g43, c[sym(2, 2)], c32);
+    c[sym(3, 2)] = c32n;
+    c[sym(3, 3)] = fma(g43, c32 + c32n, c[sym(3, 3)]);
+  }
+  // n = A_l m + (s / 2) v_l;  c += n v_l^T + v_l n^T
+  const T hs = T(0.5f) * sg;
+  const T n[5] = {fma(hs, vl0, fma(a03, m[3], fma(a02, m[2], ctt * m[0]))),
+                  fma(hs, cot, fma(f25, m[4], m[1])), m[2], fma(hs, kappa, fma(g43, m[2], m[3])),
+                  m[4]};
+  const T v[5] = {vl0, cot, T(0.f), kappa, T(0.f)};
+  constexpr unsigned VM = (1u << 0) | (1u << 1) | (1u << 3);
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      T acc = c[sym(i, j)];
+      if (VM & (1u << j)) acc = fma(n[i], v[j], acc);
+      if (VM & (1u << i)) acc = fma(v[i], n[j], acc);
+      c[sym(i, j)] = acc;
+    }
+}
+
+// Propagation to the plane z = Z.  Returns the mask of lanes whose plane is
+// behind them; if any lane fails nothing is modified.  ZFREE: the caller
+// guarantees that row and column z of c are zero (true from the first plane
+// on: z' = Z makes the z row of J vanish, and an update keeps a zero row
+// zero), so the z component of grad h meets only zeros and is skipped.
+template <bool ZFREE = false, class T>
 __device__ __forceinline__ typename Lanes<T>::M prop_z(T (&p)[6], T (&c)[21], Trig<T>& g, T dkdw,
                                                        float Z) {
   const T dz = T(Z) - p[2];
@@ -461,7 +637,7 @@ __device__ __forceinline__ typename Lanes<T>::M prop_z(T (&p)[6], T (&c)[21], Tr
   // sin phi', 0 on the plane, 0, kappa, 0)
   const T gr[6] = {T(0.f), T(0.f), -tanth, T(0.f), T(0.f), hth};
   const T v[6] = {c1, s1, T(0.f), T(0.f), kappa, T(0.f)};
-  similarity_rank1<false, (1u << 2) | (1u << 5), (1u << 0) | (1u << 1) | (1u << 4)>(
+  similarity_rank1<false, (ZFREE ? 0u : (1u << 2)) | (1u << 5), (1u << 0) | (1u << 1) | (1u << 4)>(
       c, hh * fma(sp, cm, -(s * sm)), -dy, hh * fma(sp, sm, s * cm), dx, T(0.f), h * dkdw, gr, v);
   p[0] += dx;
   p[1] += dy;
@@ -684,14 +860,14 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
 
 // Propagation to the cylinder r = R (path length from path_r).  Returns the
 // mask of lanes that cannot reach the cylinder; if any lane fails nothing is
-// modified.
-template <class T, bool SEEDED = false, Start START = Start::kAuto>
-__device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Trig<T>& g, T dkdw,
-                                                       float R, int max_iter, float tol_abs,
-                                                       bool line_start,
-                                                       unsigned (&iters)[Lanes<T>::n],
-                                                       typename Lanes<T>::M& notconv,
-                                                       T gseed = T(0.f), T h_given = T(0.f)) {
+// modified.  LOCAL: c holds the local form (to_local_r) with the null
+// direction (bc, bs), and leaves in the local form at the new point, whose
+// azimuth replaces (bc, bs); otherwise c is the 6x6 packed covariance.
+template <class T, bool SEEDED, Start START, bool LOCAL>
+__device__ __forceinline__ typename Lanes<T>::M prop_r_impl(
+    T (&p)[6], T (&c)[LOCAL ? 15 : 21], T& bc, T& bs, Trig<T>& g, T dkdw, float R, int max_iter,
+    float tol_abs, bool line_start, unsigned (&iters)[Lanes<T>::n],
+    typename Lanes<T>::M& notconv, T gseed, T h_given) {
   const T x = p[0], y = p[1];
   const T kappa = dkdw * p[3];
   PathR<T> w;
@@ -713,15 +889,28 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
   const T Yw = hh * fma(sp, sm, s * cm);
   // grad h = -grad g / (dg/dh) with g = x'^2 + y'^2 - R^2.
   const T iD = frcp(fma(px, c1, py * s1));
-  const T hx = -(px * iD), hy = -(py * iD);
   const T hw = -(fma(px, Xw, py * Yw) * iD);
   const T hp = fma(px, dy, -(py * dx)) * iD;
-  // d p'/d h = (cos phi', sin phi', cot theta, 0, kappa, 0)
-  const T gr[6] = {hx, hy, T(0.f), hw, hp, T(0.f)};
-  const T v[6] = {c1, s1, cot, T(0.f), kappa, T(0.f)};
-  similarity_rank1<true, (1u << 0) | (1u << 1) | (1u << 3) | (1u << 4),
-                   (1u << 0) | (1u << 1) | (1u << 2) | (1u << 4)>(
-      c, Xw, -dy, Yw, dx, -(h * isth * isth), h * dkdw, gr, v);
+  if constexpr (LOCAL) {
+    // the new null direction: the azimuth of the crossing
+    const T ir = frsqrt(fma(px, px, py * py));
+    const T c2 = px * ir, s2 = py * ir;
+    // A_l = P' A B: (l, l) = t'.t, (l, w) = t'.(Xw, Yw), (l, phi) = t'.(-dy, dx)
+    // with t = (-bs, bc), t' = (-s2, c2); g_l = B^T g; v_l = P' v
+    similarity_local_r(c, fma(s2, bs, c2 * bc), fma(c2, Yw, -(s2 * Xw)), fma(c2, dx, s2 * dy),
+                       -(h * isth * isth), h * dkdw, fma(bs, px, -(bc * py)) * iD, hw, hp,
+                       fma(c2, s1, -(s2 * c1)), cot, kappa);
+    bc = c2;
+    bs = s2;
+  } else {
+    const T hx = -(px * iD), hy = -(py * iD);
+    // d p'/d h = (cos phi', sin phi', cot theta, 0, kappa, 0)
+    const T gr[6] = {hx, hy, T(0.f), hw, hp, T(0.f)};
+    const T v[6] = {c1, s1, cot, T(0.f), kappa, T(0.f)};
+    similarity_rank1<true, (1u << 0) | (1u << 1) | (1u << 3) | (1u << 4),
+                     (1u << 0) | (1u << 1) | (1u << 2) | (1u << 4)>(
+        c, Xw, -dy, Yw, dx, -(h * isth * isth), h * dkdw, gr, v);
+  }
   p[0] = px;
   p[1] = py;
   p[2] = fma(h, cot, p[2]);
@@ -735,6 +924,32 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
   g.cphi = c1;
   g.sphi = s1;
   return fail;
+}
+
+template <class T, bool SEEDED = false, Start START = Start::kAuto>
+__device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Trig<T>& g, T dkdw,
+                                                       float R, int max_iter, float tol_abs,
+                                                       bool line_start,
+                                                       unsigned (&iters)[Lanes<T>::n],
+                                                       typename Lanes<T>::M& notconv,
+                                                       T gseed = T(0.f), T h_given = T(0.f)) {
+  T unused0, unused1;
+  return prop_r_impl<T, SEEDED, START, false>(p, c, unused0, unused1, g, dkdw, R, max_iter,
+                                              tol_abs, line_start, iters, notconv, gseed,
+                                              h_given);
+}
+
+// As prop_r, on the local form (cl, bc, bs) of the covariance.
+template <class T, Start START = Start::kAuto>
+__device__ __forceinline__ typename Lanes<T>::M prop_r_local(T (&p)[6], T (&cl)[15], T& bc, T& bs,
+                                                             Trig<T>& g, T dkdw, float R,
+                                                             int max_iter, float tol_abs,
+                                                             bool line_start,
+                                                             unsigned (&iters)[Lanes<T>::n],
+                                                             typename Lanes<T>::M& notconv,
+                                                             T h_given = T(0.f)) {
+  return prop_r_impl<T, false, START, true>(p, cl, bc, bs, g, dkdw, R, max_iter, tol_abs,
+                                            line_start, iters, notconv, T(0.f), h_given);
 }
 
 // Kalman update with a 2-D measurement: a and b are the columns of C H^T (the
@@ -785,7 +1000,11 @@ struct Sqrt2 {
   }
 };
 
-template <bool COMPENSATED, class T>
+//
+// SKIP marks rows whose a and b entries the caller knows to be zero (row z
+// after a p2z propagation): their parameters and covariance rows and columns
+// are left as they are, which is what the update would compute.
+template <bool COMPENSATED, unsigned SKIP = 0, class T>
 __device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], const T (&b)[6],
                                        T S00, T S01, T S11, T r0, T r1) {
   const Sqrt2<COMPENSATED, T> q(S00, S01, S11);
@@ -796,12 +1015,45 @@ __device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], c
   const T al = q.S00 * q.w1, be = q.S01 * q.w1;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
+    if (SKIP & (1u << i)) continue;
     u0[i] = a[i] * q.w0;
     u1[i] = COMPENSATED ? q.cross(b[i], a[i]) * q.w1 : fma(b[i], al, -(a[i] * be));
     p[i] = fma(u0[i], z0, fma(u1[i], z1, p[i]));
   }
 #pragma unroll
   for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      if ((SKIP & (1u << i)) || (SKIP & (1u << j))) continue;
+      c[sym(i, j)] = fma(-u0[i], u0[j], fma(-u1[i], u1[j], c[sym(i, j)]));
+    }
+  return chi2;
+}
+
+// kalman_2d on the local form of a p2r covariance (to_local_r), whose first
+// measured direction projects onto l with the factor chp: a = chp c_l (c_l
+// the l column of c), b = c_z.  chp is folded into the scalars, and the l
+// component of the parameter change moves the position along (-bs, bc).
+template <class T>
+__device__ __forceinline__ T kalman_2d_local(T (&p)[6], T (&c)[15], T bc, T bs, T chp, T S00,
+                                             T S01, T S11, T r0, T r1) {
+  const Sqrt2<false, T> q(S00, S01, S11);
+  T z0, z1;
+  const T chi2 = q.chi2(r0, r1, z0, z1);
+  const T w0 = chp * q.w0, al = q.S00 * q.w1, be = chp * (q.S01 * q.w1);
+  T u0[5], u1[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    u0[i] = c[sym(i, 0)] * w0;
+    u1[i] = fma(c[sym(i, 1)], al, -(c[sym(i, 0)] * be));
+  }
+  const T dl = fma(u0[0], z0, u1[0] * z1);
+  p[0] = fma(-bs, dl, p[0]);
+  p[1] = fma(bc, dl, p[1]);
+#pragma unroll
+  for (int i = 1; i < 5; ++i) p[i + 1] = fma(u0[i], z0, fma(u1[i], z1, p[i + 1]));
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
 #pragma unroll
     for (int j = 0; j <= i; ++j) c[sym(i, j)] = fma(-u0[i], u0[j], fma(-u1[i], u1[j], c[sym(i, j)]));
   return chi2;
@@ -811,9 +1063,12 @@ __device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], c
 // angles (given their values before the update), wrap phi into (-pi, pi], and
 // flip the charge (qf = +-1 per lane) where w became negative.  Returns the
 // mask of flipped lanes.
-template <class T>
-__device__ __forceinline__ typename Lanes<T>::M normalise(T (&p)[6], T (&c)[21], T& qf,
+// NC = 21: the 6x6 covariance; NC = 15: the p2r local form (w is its third
+// coordinate).
+template <int NC, class T>
+__device__ __forceinline__ typename Lanes<T>::M normalise(T (&p)[6], T (&c)[NC], T& qf,
                                                           Trig<T>& g, T phi_before, T th_before) {
+  constexpr int D = NC == 21 ? 6 : 5, W = NC == 21 ? 3 : 2;
   turn_by2(g.cphi, g.sphi, p[4] - phi_before, g.cth, g.sth, p[5] - th_before);
   const T k = floor_((pi_<T>() - p[4]) * inv_two_pi_<T>());
   p[4] = fma(k, two_pi_<T>(), p[4]);
@@ -823,14 +1078,15 @@ __device__ __forceinline__ typename Lanes<T>::M normalise(T (&p)[6], T (&c)[21],
     p[3] = p[3] * sgn;
     qf = qf * sgn;
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
-      if (i != 3) c[sym(3, i)] = c[sym(3, i)] * sgn;
+    for (int i = 0; i < D; ++i)
+      if (i != W) c[sym(W, i)] = c[sym(W, i)] * sgn;
   }
   return flip;
 }
 
-// p2z update: H measures x and y.
-template <class T>
+// p2z update: H measures x and y.  ZFREE: row and column z of c are zero
+// (every update follows a propagation to a plane).
+template <bool ZFREE = false, class T>
 __device__ __forceinline__ T update_z(T (&p)[6], T (&c)[21], const T (&m)[3], const T (&v)[6]) {
   T a[6], b[6];
 #pragma unroll
@@ -838,8 +1094,8 @@ __device__ __forceinline__ T update_z(T (&p)[6], T (&c)[21], const T (&m)[3], co
     a[i] = c[sym(i, 0)];
     b[i] = c[sym(i, 1)];
   }
-  return kalman_2d<true>(p, c, a, b, a[0] + v[0], b[0] + v[1], b[1] + v[2], m[0] - p[0],
-                         m[1] - p[1]);
+  return kalman_2d<true, ZFREE ? (1u << 2) : 0u>(p, c, a, b, a[0] + v[0], b[0] + v[1],
+                                                 b[1] + v[2], m[0] - p[0], m[1] - p[1]);
 }
 
 // p2r update: H measures the position along the cylinder's azimuthal
@@ -862,6 +1118,46 @@ __device__ __forceinline__ T update_r(T (&p)[6], T (&c)[21], const T (&m)[3], co
   const T r0 = fma(ch, m[1] - p[1], -(sh * (m[0] - p[0])));
   const T r1 = m[2] - p[2];
   return kalman_2d<false>(p, c, a, b, S00, S01, S11, r0, r1);
+}
+
+// The p2r measurement against the local form (cl, bc, bs): the azimuthal
+// measurement direction t_h projects onto l with chp = t_h . (-bs, bc), the
+// cosine of the angle between the hit's azimuth and the basis azimuth.
+// Shared by update_r_local and chi2_r_local, so that the chi2 of a chosen
+// candidate is the one its update returns.
+template <class T>
+struct MeasR {
+  T chp, S00, S01, S11, r0, r1;
+  __device__ __forceinline__ MeasR(const T (&p)[6], const T (&cl)[15], T bc, T bs,
+                                   const T (&m)[3], const T (&v)[6]) {
+    const T ir = frsqrt(fma(m[0], m[0], m[1] * m[1]));
+    const T sh = m[1] * ir, ch = m[0] * ir;
+    chp = fma(sh, bs, ch * bc);
+    const T vtt = fma(sh * sh, v[0], fma(ch * ch, v[2], T(-2.f) * sh * ch * v[1]));
+    const T vtz = fma(ch, v[4], -(sh * v[3]));
+    S00 = fma(chp * chp, cl[sym(0, 0)], vtt);
+    S01 = fma(chp, cl[sym(1, 0)], vtz);
+    S11 = cl[sym(1, 1)] + v[5];
+    r0 = fma(ch, m[1] - p[1], -(sh * (m[0] - p[0])));
+    r1 = m[2] - p[2];
+  }
+};
+
+// update_r on the local form (cl, bc, bs).
+template <class T>
+__device__ __forceinline__ T update_r_local(T (&p)[6], T (&cl)[15], T bc, T bs, const T (&m)[3],
+                                            const T (&v)[6]) {
+  const MeasR<T> h(p, cl, bc, bs, m, v);
+  return kalman_2d_local(p, cl, bc, bs, h.chp, h.S00, h.S01, h.S11, h.r0, h.r1);
+}
+
+// chi2 of a hit against the prediction in the local form, without the update.
+template <class T>
+__device__ __forceinline__ T chi2_r_local(const T (&p)[6], const T (&cl)[15], T bc, T bs,
+                                          const T (&m)[3], const T (&v)[6]) {
+  const MeasR<T> h(p, cl, bc, bs, m, v);
+  T z0, z1;
+  return Sqrt2<false, T>(h.S00, h.S01, h.S11).chi2(h.r0, h.r1, z0, z1);
 }
 
 // chi2 = r^T S^-1 r of a hit against the prediction, without the update
