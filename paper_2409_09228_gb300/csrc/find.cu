@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
   // the exact form costs the loop nothing (inside it, 20 %).
   int l = 0;
   bool propagated = false;  // layer l's propagation is done
+  T lag = T(0.f);           // p2r: how far (g.cphi, g.sphi) trails p[4] (prop_r_local)
   for (;;) {
     bool rerun = false;
     for (; l < a.nlayer; ++l) {
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
       else
         failed = fitk::prop_r_local<T, fitk::Start::kFast>(p, cl, bc, bs, g, dkdw, sf,
                                                            geo.max_iter, geo.tol * sf,
-                                                           geo.line_start, iters, nc);
+                                                           geo.line_start, iters, nc, lag);
       if (failed) {
         if (MODE == FIT_MODE_R && !geo.line_start)
           rerun = true;
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
           flip = fitk::normalise(p, c, qf, g, phi_pred, th_pred);
         } else {
           x2 = fitk::update_r_local(p, cl, bc, bs, m, v);
-          flip = fitk::normalise(p, cl, qf, g, phi_pred, th_pred);
+          flip = fitk::normalise(p, cl, qf, g, phi_pred, th_pred, lag);
         }
         if (flip) st |= FIT_ST_CHARGE_FLIP;
         if (!fitk::finite_(x2)) {
@@ -145,6 +146,8 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
           ++l;
           break;
         }
+      } else if (MODE == FIT_MODE_R) {
+        fitk::turn_by(g.cphi, g.sphi, lag);  // no update: the propagation's own turn
       }
       chi2 += x2;
       if (a.chi2_layer) a.chi2_layer[(int64_t)l * a.ld_out + t] = x2;
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
     const T h0 = fitk::crossing_exact<T>(p[0], p[1], g.cphi, g.sphi, dkdw * p[3], T(sf));
     bool nc = false;
     if (fitk::prop_r_local<T, fitk::Start::kGiven>(p, cl, bc, bs, g, dkdw, sf, geo.max_iter,
-                                                   geo.tol * sf, false, iters, nc, h0)) {
+                                                   geo.tol * sf, false, iters, nc, lag, h0)) {
       st |= FIT_ST_NO_INTERSECTION;
       break;
     }

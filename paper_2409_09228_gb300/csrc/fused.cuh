@@ -178,11 +178,12 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
     const float sf = geo.surf.s[l];
     const T dkdw = s.qf * T(-geo.kB);
     M fail, nc = fitk::lt(T(1.f), T(0.f));
+    T lag = T(0.f);
     if (MODE == FIT_MODE_Z)
       fail = fitk::prop_z<true>(s.p, s.c, s.g, dkdw, sf);
     else
       fail = fitk::prop_r_local(s.p, s.cl, s.bc, s.bs, s.g, dkdw, sf, geo.max_iter,
-                                geo.tol * sf, geo.line_start, iters, nc);
+                                geo.tol * sf, geo.line_start, iters, nc, lag);
     if (fitk::any(fitk::and_(fail, alive))) return done(l);
     const T phi_pred = s.p[4], th_pred = s.p[5];
     T x2;
@@ -192,7 +193,7 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
       flip = fitk::normalise(s.p, s.c, s.qf, s.g, phi_pred, th_pred);
     } else {
       x2 = fitk::update_r_local(s.p, s.cl, s.bc, s.bs, m, v);
-      flip = fitk::normalise(s.p, s.cl, s.qf, s.g, phi_pred, th_pred);
+      flip = fitk::normalise(s.p, s.cl, s.qf, s.g, phi_pred, th_pred, lag);
     }
     alive = fitk::and_(alive, fitk::finite_(x2));
     any_nc = fitk::or_(any_nc, nc);

@@ -863,11 +863,14 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
 // modified.  LOCAL: c holds the local form (to_local_r) with the null
 // direction (bc, bs), and leaves in the local form at the new point, whose
 // azimuth replaces (bc, bs); otherwise c is the 6x6 packed covariance.
+// LOCAL also leaves the direction (g.cphi, g.sphi) at the angle of the last
+// evaluation, lag = kappa d short of p[4]: the caller turns it on with the
+// update's change of phi (normalise), one turn instead of two.
 template <class T, bool SEEDED, Start START, bool LOCAL>
 __device__ __forceinline__ typename Lanes<T>::M prop_r_impl(
     T (&p)[6], T (&c)[LOCAL ? 15 : 21], T& bc, T& bs, Trig<T>& g, T dkdw, float R, int max_iter,
     float tol_abs, bool line_start, unsigned (&iters)[Lanes<T>::n],
-    typename Lanes<T>::M& notconv, T gseed, T h_given) {
+    typename Lanes<T>::M& notconv, T gseed, T h_given, T& lag) {
   const T x = p[0], y = p[1];
   const T kappa = dkdw * p[3];
   PathR<T> w;
@@ -915,12 +918,16 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r_impl(
   p[1] = py;
   p[2] = fma(h, cot, p[2]);
   p[4] = fma(kappa, h, p[4]);
-  // the last step d is below the tolerance on converged lanes, so kappa d
-  // is far inside the series' range and needs no range test
-  if (!any(notconv))
-    turn_small(c1, s1, kappa * d);
-  else
-    turn_by(c1, s1, kappa * d);
+  if constexpr (LOCAL) {
+    lag = kappa * d;
+  } else {
+    // the last step d is below the tolerance on converged lanes, so kappa d
+    // is far inside the series' range and needs no range test
+    if (!any(notconv))
+      turn_small(c1, s1, kappa * d);
+    else
+      turn_by(c1, s1, kappa * d);
+  }
   g.cphi = c1;
   g.sphi = s1;
   return fail;
@@ -933,13 +940,14 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
                                                        unsigned (&iters)[Lanes<T>::n],
                                                        typename Lanes<T>::M& notconv,
                                                        T gseed = T(0.f), T h_given = T(0.f)) {
-  T unused0, unused1;
+  T unused0, unused1, unused2;
   return prop_r_impl<T, SEEDED, START, false>(p, c, unused0, unused1, g, dkdw, R, max_iter,
                                               tol_abs, line_start, iters, notconv, gseed,
-                                              h_given);
+                                              h_given, unused2);
 }
 
-// As prop_r, on the local form (cl, bc, bs) of the covariance.
+// As prop_r, on the local form (cl, bc, bs) of the covariance; the direction
+// (g.cphi, g.sphi) is left lag short of p[4] (see prop_r_impl).
 template <class T, Start START = Start::kAuto>
 __device__ __forceinline__ typename Lanes<T>::M prop_r_local(T (&p)[6], T (&cl)[15], T& bc, T& bs,
                                                              Trig<T>& g, T dkdw, float R,
@@ -947,9 +955,9 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r_local(T (&p)[6], T (&cl)[
                                                              bool line_start,
                                                              unsigned (&iters)[Lanes<T>::n],
                                                              typename Lanes<T>::M& notconv,
-                                                             T h_given = T(0.f)) {
+                                                             T& lag, T h_given = T(0.f)) {
   return prop_r_impl<T, false, START, true>(p, cl, bc, bs, g, dkdw, R, max_iter, tol_abs,
-                                            line_start, iters, notconv, T(0.f), h_given);
+                                            line_start, iters, notconv, T(0.f), h_given, lag);
 }
 
 // Kalman update with a 2-D measurement: a and b are the columns of C H^T (the
@@ -1064,12 +1072,13 @@ __device__ __forceinline__ T kalman_2d_local(T (&p)[6], T (&c)[15], T bc, T bs, 
 // flip the charge (qf = +-1 per lane) where w became negative.  Returns the
 // mask of flipped lanes.
 // NC = 21: the 6x6 covariance; NC = 15: the p2r local form (w is its third
-// coordinate).
+// coordinate).  lag: how far (g.cphi, g.sphi) was behind phi_before.
 template <int NC, class T>
 __device__ __forceinline__ typename Lanes<T>::M normalise(T (&p)[6], T (&c)[NC], T& qf,
-                                                          Trig<T>& g, T phi_before, T th_before) {
+                                                          Trig<T>& g, T phi_before, T th_before,
+                                                          T lag = T(0.f)) {
   constexpr int D = NC == 21 ? 6 : 5, W = NC == 21 ? 3 : 2;
-  turn_by2(g.cphi, g.sphi, p[4] - phi_before, g.cth, g.sth, p[5] - th_before);
+  turn_by2(g.cphi, g.sphi, (p[4] - phi_before) + lag, g.cth, g.sth, p[5] - th_before);
   const T k = floor_((pi_<T>() - p[4]) * inv_two_pi_<T>());
   p[4] = fma(k, two_pi_<T>(), p[4]);
   const auto flip = lt(p[3], T(0.f));
