@@ -752,6 +752,7 @@ enum class Start { kAuto, kFast, kGiven };
 template <class T>
 struct PathR {
   T h, d, u, s, cu, sp, cm, sm, px, py, c1, s1;
+  T ib;  // 1 / b, b = (px, py) . (c1, s1)
 };
 
 // Path length to the cylinder r = R by straight-line steps along the current
@@ -825,7 +826,7 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
   // only one, and peeled it is 3 % faster); max_iter >= 1.
   M conv = lt(T(1.f), T(0.f));  // all false
   T u = T(0.f), s = T(1.f), cu = T(1.f), sp = T(0.f), sm = sph, cm = cph, px = x, py = y, c1 = cph,
-    s1 = sph, d = T(0.f);
+    s1 = sph, d = T(0.f), ib = T(0.f);
   auto step = [&]() {
 #pragma unroll
     for (int i = 0; i < Lanes<T>::n; ++i) iters[i] += Lanes<T>::get(conv, i) ? 0u : 1u;
@@ -844,9 +845,18 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
     // Step along (c1, s1) to the circle: d^2 + 2 b d + c2 = 0, smaller root.
     const T b = fma(px, c1, py * s1);
     const T c2 = fma(px, px, fma(py, py, -R2));
-    const T disc = fma(b, b, -c2);
-    // where the line misses the circle (disc < 0) the Newton step -c2 / (2 b)
-    d = fdiv(-c2, sel(le(T(0.f), disc), b + copysign_(fsqrt(disc), b), T(2.f) * b));
+    ib = frcp(b);
+    if (all(le(fabs_(c2), T(1e-4f) * (b * b)))) {
+      // Close to the circle the root is -c2 / (2 b) (1 + c2 / (4 b^2) + ...):
+      // the dropped factor is below 2.5e-5 relative, on a step below
+      // 5e-5 |b|; on a converged step (|d| <= tol) it moves h by less than
+      // 1e-12 R^2 / |b|, far below FP32 resolution.
+      d = T(-0.5f) * c2 * ib;
+    } else {
+      const T disc = fma(b, b, -c2);
+      // where the line misses the circle (disc < 0) the Newton step -c2 / (2 b)
+      d = fdiv(-c2, sel(le(T(0.f), disc), b + copysign_(fsqrt(disc), b), T(2.f) * b));
+    }
     d = sel(conv, T(0.f), d);
     h += d;
     conv = or_(conv, le(fabs_(d), T(tol_abs)));
@@ -854,7 +864,7 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
   step();
   for (int it = 1; it < max_iter && !all(conv); ++it) step();
   notconv = not_(conv);
-  w = {h, d, u, s, cu, sp, cm, sm, px, py, c1, s1};
+  w = {h, d, u, s, cu, sp, cm, sm, px, py, c1, s1, ib};
   return fail;
 }
 
@@ -890,8 +900,14 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r_impl(
   const T hh = T(0.5f) * h * h * dkdw;
   const T Xw = hh * fma(sp, cm, -(s * sm));
   const T Yw = hh * fma(sp, sm, s * cm);
-  // grad h = -grad g / (dg/dh) with g = x'^2 + y'^2 - R^2.
-  const T iD = frcp(fma(px, c1, py * s1));
+  // grad h = -grad g / (dg/dh) with g = x'^2 + y'^2 - R^2.  dg/dh / 2 =
+  // (px, py) . (c1, s1) = b + d with b the last evaluation's: on converged
+  // lanes (|d| <= tol) 1 / (b + d) = ib (1 - d ib) to within (d ib)^2.
+  T iD;
+  if (!any(notconv))
+    iD = fma(-(d * w.ib), w.ib, w.ib);
+  else
+    iD = frcp(fma(px, c1, py * s1));
   const T hw = -(fma(px, Xw, py * Yw) * iD);
   const T hp = fma(px, dy, -(py * dx)) * iD;
   if constexpr (LOCAL) {
