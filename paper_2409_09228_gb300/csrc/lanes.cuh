@@ -51,17 +51,23 @@ __device__ __forceinline__ F2 frcp(F2 x) { return F2(frcp(x.v.x), frcp(x.v.y)); 
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 // a * (1/b): the reciprocals per lane, the product packed
 __device__ __forceinline__ F2 fdiv(F2 a, F2 b) { return a * frcp(b); }
-// Approximate square root (one MUFU operation, relative error ~2^-23); NaN
-// for x < 0, which every caller either excludes by its own test or sends
-// down a failing branch.
+// Approximate square root and reciprocal square root (one MUFU operation
+// each, relative error ~2^-23); NaN for x < 0, which every caller either
+// excludes by its own test or sends down a failing branch.  Subnormal
+// inputs flush to zero (.ftz): the fit's quantities are far from 1e-38, and
+// the subnormal-safe forms cost a test and two multiplies around each MUFU.
 __device__ __forceinline__ float fsqrt(float x) {
   float r;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 __device__ __forceinline__ F2 fsqrt(F2 x) { return F2(fsqrt(x.v.x), fsqrt(x.v.y)); }
-__device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ F2 frsqrt(F2 x) { return F2(rsqrtf(x.v.x), rsqrtf(x.v.y)); }
+__device__ __forceinline__ float frsqrt(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ F2 frsqrt(F2 x) { return F2(frsqrt(x.v.x), frsqrt(x.v.y)); }
 __device__ __forceinline__ float fabs_(float x) { return fabsf(x); }
 __device__ __forceinline__ F2 fabs_(F2 x) { return F2(fabsf(x.v.x), fabsf(x.v.y)); }
 __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
