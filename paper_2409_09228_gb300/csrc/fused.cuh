@@ -158,7 +158,21 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
   // lanes that hit max_iter or flipped charge on some layer; the status bits
   // (with non-finite for lanes no longer alive) are set once, on return
   M any_nc = fitk::lt(T(1.f), T(0.f)), any_flip = any_nc;
+  // p2r: the last update's covariance part (cl -= pu0 pu0^T + pu1 pu1^T),
+  // applied while the next propagation computes its path length (whose
+  // serial chain leaves the FMA pipe idle), or on return
+  T pu0[5], pu1[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) pu0[k] = pu1[k] = T(0.f);
+  auto settle = [&]() {
+    if (MODE == FIT_MODE_R) {
+      fitk::downdate_local(s.cl, pu0, pu1);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) pu0[k] = pu1[k] = T(0.f);
+    }
+  };
   auto done = [&](int r) {
+    settle();
 #pragma unroll
     for (int i = 0; i < Lanes<T>::n; ++i) {
       if (Lanes<T>::get(any_nc, i)) st[i] |= FIT_ST_NOT_CONVERGED;
@@ -183,7 +197,7 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
       fail = fitk::prop_z<true>(s.p, s.c, s.g, dkdw, sf);
     else
       fail = fitk::prop_r_local(s.p, s.cl, s.bc, s.bs, s.g, dkdw, sf, geo.max_iter,
-                                geo.tol * sf, geo.line_start, iters, nc, lag);
+                                geo.tol * sf, geo.line_start, iters, nc, lag, T(0.f), settle);
     if (fitk::any(fitk::and_(fail, alive))) return done(l);
     const T phi_pred = s.p[4], th_pred = s.p[5];
     T x2;
@@ -192,8 +206,13 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
       x2 = fitk::update_z<true>(s.p, s.c, m, v);
       flip = fitk::normalise(s.p, s.c, s.qf, s.g, phi_pred, th_pred);
     } else {
-      x2 = fitk::update_r_local(s.p, s.cl, s.bc, s.bs, m, v);
+      x2 = fitk::update_r_local_deferred(s.p, s.cl, s.bc, s.bs, m, v, pu0, pu1);
       flip = fitk::normalise(s.p, s.cl, s.qf, s.g, phi_pred, th_pred, lag);
+      if (fitk::any(flip)) {  // the flip negates row w of the pending part too
+        const T sgn = fitk::sel(flip, T(-1.f), T(1.f));
+        pu0[2] = pu0[2] * sgn;
+        pu1[2] = pu1[2] * sgn;
+      }
     }
     alive = fitk::and_(alive, fitk::finite_(x2));
     any_nc = fitk::or_(any_nc, nc);

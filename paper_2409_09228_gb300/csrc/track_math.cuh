@@ -775,13 +775,19 @@ struct PathR {
 // h_line when the start is inside the cylinder and that value is finite and
 // within h_line / 4 of h_line.  The iteration, its tolerance and its result
 // are otherwise unchanged.
-template <class T, bool SEEDED = false, Start START = Start::kAuto>
+// Nothing to overlap (path_r's default).
+struct NoOverlap {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+template <class T, bool SEEDED = false, Start START = Start::kAuto, class Overlap = NoOverlap>
 __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Trig<T>& g, T kappa,
                                                        float R, int max_iter, float tol_abs,
                                                        bool line_start,
                                                        unsigned (&iters)[Lanes<T>::n],
                                                        typename Lanes<T>::M& notconv, PathR<T>& w,
-                                                       T gseed = T(0.f), T h_given = T(0.f)) {
+                                                       T gseed = T(0.f), T h_given = T(0.f),
+                                                       const Overlap& ov = Overlap()) {
   using M = typename Lanes<T>::M;
   const T sph = g.sphi, cph = g.cphi;
   const T x = p[0], y = p[1];
@@ -792,11 +798,15 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
   const M inside = le(c0, T(0.f));
   T h;
   M fail;
+  // ov: independent work of the caller, run once, in the same straight-line
+  // code as the start's serial chain so that the two can interleave
   if constexpr (START == Start::kGiven) {
+    ov();
     h = h_given;
     fail = not_(lt(T(0.f), h));
     if (any(fail)) return fail;
   } else if (SEEDED || line_start) {
+    ov();
     // The transverse circle (centre c, radius rho = 1/|kappa|) reaches radius
     // R only if |c| + rho >= R, which always holds when rho >= R.
     fail = lt(T(1.f), T(R) * fabs_(kappa));
@@ -817,6 +827,7 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
       h = sel(and_(and_(inside, finite_(hs)), le(fabs_(hs - h), T(0.25f) * h)), hs, h);
     }
   } else {
+    ov();
     fail = crossing_start<T, START == Start::kAuto>(x, y, cph, sph, kappa, R, b0, c0, h);
     if (any(fail)) return fail;
   }
@@ -876,16 +887,16 @@ __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Tr
 // LOCAL also leaves the direction (g.cphi, g.sphi) at the angle of the last
 // evaluation, lag = kappa d short of p[4]: the caller turns it on with the
 // update's change of phi (normalise), one turn instead of two.
-template <class T, bool SEEDED, Start START, bool LOCAL>
+template <class T, bool SEEDED, Start START, bool LOCAL, class Overlap = NoOverlap>
 __device__ __forceinline__ typename Lanes<T>::M prop_r_impl(
     T (&p)[6], T (&c)[LOCAL ? 15 : 21], T& bc, T& bs, Trig<T>& g, T dkdw, float R, int max_iter,
     float tol_abs, bool line_start, unsigned (&iters)[Lanes<T>::n],
-    typename Lanes<T>::M& notconv, T gseed, T h_given, T& lag) {
+    typename Lanes<T>::M& notconv, T gseed, T h_given, T& lag, const Overlap& ov = Overlap()) {
   const T x = p[0], y = p[1];
   const T kappa = dkdw * p[3];
   PathR<T> w;
   const auto fail = path_r<T, SEEDED, START>(p, g, kappa, R, max_iter, tol_abs, line_start,
-                                             iters, notconv, w, gseed, h_given);
+                                             iters, notconv, w, gseed, h_given, ov);
   if (any(fail)) return fail;
   const T h = w.h, d = w.d, s = w.s, sp = w.sp, cm = w.cm, sm = w.sm;
   T px = w.px, py = w.py, c1 = w.c1, s1 = w.s1;
@@ -963,17 +974,19 @@ __device__ __forceinline__ typename Lanes<T>::M prop_r(T (&p)[6], T (&c)[21], Tr
 }
 
 // As prop_r, on the local form (cl, bc, bs) of the covariance; the direction
-// (g.cphi, g.sphi) is left lag short of p[4] (see prop_r_impl).
-template <class T, Start START = Start::kAuto>
+// (g.cphi, g.sphi) is left lag short of p[4] (see prop_r_impl).  ov: work
+// independent of the path length, overlapped with its start (path_r).
+template <class T, Start START = Start::kAuto, class Overlap = NoOverlap>
 __device__ __forceinline__ typename Lanes<T>::M prop_r_local(T (&p)[6], T (&cl)[15], T& bc, T& bs,
                                                              Trig<T>& g, T dkdw, float R,
                                                              int max_iter, float tol_abs,
                                                              bool line_start,
                                                              unsigned (&iters)[Lanes<T>::n],
                                                              typename Lanes<T>::M& notconv,
-                                                             T& lag, T h_given = T(0.f)) {
+                                                             T& lag, T h_given = T(0.f),
+                                                             const Overlap& ov = Overlap()) {
   return prop_r_impl<T, false, START, true>(p, cl, bc, bs, g, dkdw, R, max_iter, tol_abs,
-                                            line_start, iters, notconv, T(0.f), h_given, lag);
+                                            line_start, iters, notconv, T(0.f), h_given, lag, ov);
 }
 
 // Kalman update with a 2-D measurement: a and b are the columns of C H^T (the
@@ -1054,18 +1067,29 @@ __device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], c
   return chi2;
 }
 
+// c -= u0 u0^T + u1 u1^T on the local form.
+template <class T>
+__device__ __forceinline__ void downdate_local(T (&c)[15], const T (&u0)[5], const T (&u1)[5]) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) c[sym(i, j)] = fma(-u0[i], u0[j], fma(-u1[i], u1[j], c[sym(i, j)]));
+}
+
 // kalman_2d on the local form of a p2r covariance (to_local_r), whose first
 // measured direction projects onto l with the factor chp: a = chp c_l (c_l
 // the l column of c), b = c_z.  chp is folded into the scalars, and the l
 // component of the parameter change moves the position along (-bs, bc).
-template <class T>
+// DEFER: the covariance part, c -= u0 u0^T + u1 u1^T, is left to the caller
+// (downdate_local), which can then overlap it with the serial start of the
+// next propagation; u0 and u1 are returned either way.
+template <bool DEFER = false, class T>
 __device__ __forceinline__ T kalman_2d_local(T (&p)[6], T (&c)[15], T bc, T bs, T chp, T S00,
-                                             T S01, T S11, T r0, T r1) {
+                                             T S01, T S11, T r0, T r1, T (&u0)[5], T (&u1)[5]) {
   const Sqrt2<false, T> q(S00, S01, S11);
   T z0, z1;
   const T chi2 = q.chi2(r0, r1, z0, z1);
   const T w0 = chp * q.w0, al = q.S00 * q.w1, be = chp * (q.S01 * q.w1);
-  T u0[5], u1[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     u0[i] = c[sym(i, 0)] * w0;
@@ -1076,10 +1100,7 @@ __device__ __forceinline__ T kalman_2d_local(T (&p)[6], T (&c)[15], T bc, T bs, 
   p[1] = fma(bc, dl, p[1]);
 #pragma unroll
   for (int i = 1; i < 5; ++i) p[i + 1] = fma(u0[i], z0, fma(u1[i], z1, p[i + 1]));
-#pragma unroll
-  for (int i = 0; i < 5; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j) c[sym(i, j)] = fma(-u0[i], u0[j], fma(-u1[i], u1[j], c[sym(i, j)]));
+  if constexpr (!DEFER) downdate_local(c, u0, u1);
   return chi2;
 }
 
@@ -1173,7 +1194,17 @@ template <class T>
 __device__ __forceinline__ T update_r_local(T (&p)[6], T (&cl)[15], T bc, T bs, const T (&m)[3],
                                             const T (&v)[6]) {
   const MeasR<T> h(p, cl, bc, bs, m, v);
-  return kalman_2d_local(p, cl, bc, bs, h.chp, h.S00, h.S01, h.S11, h.r0, h.r1);
+  T u0[5], u1[5];
+  return kalman_2d_local(p, cl, bc, bs, h.chp, h.S00, h.S01, h.S11, h.r0, h.r1, u0, u1);
+}
+// The same with the covariance part deferred: cl -= u0 u0^T + u1 u1^T is
+// the caller's (downdate_local).
+template <class T>
+__device__ __forceinline__ T update_r_local_deferred(T (&p)[6], T (&cl)[15], T bc, T bs,
+                                                     const T (&m)[3], const T (&v)[6],
+                                                     T (&u0)[5], T (&u1)[5]) {
+  const MeasR<T> h(p, cl, bc, bs, m, v);
+  return kalman_2d_local<true>(p, cl, bc, bs, h.chp, h.S00, h.S01, h.S11, h.r0, h.r1, u0, u1);
 }
 
 // chi2 of a hit against the prediction in the local form, without the update.
