@@ -158,18 +158,21 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
   // lanes that hit max_iter or flipped charge on some layer; the status bits
   // (with non-finite for lanes no longer alive) are set once, on return
   M any_nc = fitk::lt(T(1.f), T(0.f)), any_flip = any_nc;
-  // p2r: the last update's covariance part (cl -= pu0 pu0^T + pu1 pu1^T),
-  // applied while the next propagation computes its path length (whose
-  // serial chain leaves the FMA pipe idle), or on return
-  T pu0[5], pu1[5];
+  // The last update's covariance part (c -= pu0 pu0^T + pu1 pu1^T),
+  // applied while the next propagation starts (its path length, a serial
+  // chain that leaves the FMA pipe idle), or on return.  p2r: the local
+  // form's 5 rows; p2z: the 6x6 rows but z.
+  constexpr int NU = MODE == FIT_MODE_R ? 5 : 6;
+  T pu0[NU], pu1[NU];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) pu0[k] = pu1[k] = T(0.f);
+  for (int k = 0; k < NU; ++k) pu0[k] = pu1[k] = T(0.f);
   auto settle = [&]() {
-    if (MODE == FIT_MODE_R) {
+    if constexpr (MODE == FIT_MODE_R)
       fitk::downdate_local(s.cl, pu0, pu1);
+    else
+      fitk::downdate6<(1u << 2)>(s.c, pu0, pu1);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) pu0[k] = pu1[k] = T(0.f);
-    }
+    for (int k = 0; k < NU; ++k) pu0[k] = pu1[k] = T(0.f);
   };
   auto done = [&](int r) {
     settle();
@@ -194,7 +197,7 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
     M fail, nc = fitk::lt(T(1.f), T(0.f));
     T lag = T(0.f);
     if (MODE == FIT_MODE_Z)
-      fail = fitk::prop_z<true>(s.p, s.c, s.g, dkdw, sf);
+      fail = fitk::prop_z<true>(s.p, s.c, s.g, dkdw, sf, settle);
     else
       fail = fitk::prop_r_local(s.p, s.cl, s.bc, s.bs, s.g, dkdw, sf, geo.max_iter,
                                 geo.tol * sf, geo.line_start, iters, nc, lag, T(0.f), settle);
@@ -202,17 +205,18 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
     const T phi_pred = s.p[4], th_pred = s.p[5];
     T x2;
     M flip;
-    if (MODE == FIT_MODE_Z) {
-      x2 = fitk::update_z<true>(s.p, s.c, m, v);
+    if constexpr (MODE == FIT_MODE_Z) {
+      x2 = fitk::update_z_deferred(s.p, s.c, m, v, pu0, pu1);
       flip = fitk::normalise(s.p, s.c, s.qf, s.g, phi_pred, th_pred);
     } else {
       x2 = fitk::update_r_local_deferred(s.p, s.cl, s.bc, s.bs, m, v, pu0, pu1);
       flip = fitk::normalise(s.p, s.cl, s.qf, s.g, phi_pred, th_pred, lag);
-      if (fitk::any(flip)) {  // the flip negates row w of the pending part too
-        const T sgn = fitk::sel(flip, T(-1.f), T(1.f));
-        pu0[2] = pu0[2] * sgn;
-        pu1[2] = pu1[2] * sgn;
-      }
+    }
+    if (fitk::any(flip)) {  // the flip negates row w of the pending part too
+      constexpr int W = MODE == FIT_MODE_R ? 2 : 3;
+      const T sgn = fitk::sel(flip, T(-1.f), T(1.f));
+      pu0[W] = pu0[W] * sgn;
+      pu1[W] = pu1[W] * sgn;
     }
     alive = fitk::and_(alive, fitk::finite_(x2));
     any_nc = fitk::or_(any_nc, nc);

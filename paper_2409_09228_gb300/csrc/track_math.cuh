@@ -251,6 +251,11 @@ __device__ __forceinline__ void turn_by2(double& c1, double& s1, double d1, doub
   turn_by(c2, s2, d2);
 }
 
+// Nothing to overlap (the default of the propagations' ov argument).
+struct NoOverlap {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // Cosine and sine of phi and theta, carried with the track.
 template <class T>
 struct Trig {
@@ -612,9 +617,10 @@ __device__ __forceinline__ void similarity_local_r(T (&c)[15], T ctt, T a02, T a
 // guarantees that row and column z of c are zero (true from the first plane
 // on: z' = Z makes the z row of J vanish, and an update keeps a zero row
 // zero), so the z component of grad h meets only zeros and is skipped.
-template <bool ZFREE = false, class T>
+template <bool ZFREE = false, class T, class Overlap = NoOverlap>
 __device__ __forceinline__ typename Lanes<T>::M prop_z(T (&p)[6], T (&c)[21], Trig<T>& g, T dkdw,
-                                                       float Z) {
+                                                       float Z, const Overlap& ov = Overlap()) {
+  ov();  // the caller's independent work, beside the path length's reciprocal
   const T dz = T(Z) - p[2];
   const T tanth = fdiv(g.sth, g.cth);
   const T h = dz * tanth;
@@ -775,11 +781,6 @@ struct PathR {
 // h_line when the start is inside the cylinder and that value is finite and
 // within h_line / 4 of h_line.  The iteration, its tolerance and its result
 // are otherwise unchanged.
-// Nothing to overlap (path_r's default).
-struct NoOverlap {
-  __device__ __forceinline__ void operator()() const {}
-};
-
 template <class T, bool SEEDED = false, Start START = Start::kAuto, class Overlap = NoOverlap>
 __device__ __forceinline__ typename Lanes<T>::M path_r(const T (&p)[6], const Trig<T>& g, T kappa,
                                                        float R, int max_iter, float tol_abs,
@@ -1041,13 +1042,25 @@ struct Sqrt2 {
 // SKIP marks rows whose a and b entries the caller knows to be zero (row z
 // after a p2z propagation): their parameters and covariance rows and columns
 // are left as they are, which is what the update would compute.
-template <bool COMPENSATED, unsigned SKIP = 0, class T>
+// c -= u0 u0^T + u1 u1^T on the 6x6 form, rows in SKIP left alone.
+template <unsigned SKIP, class T>
+__device__ __forceinline__ void downdate6(T (&c)[21], const T (&u0)[6], const T (&u1)[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      if ((SKIP & (1u << i)) || (SKIP & (1u << j))) continue;
+      c[sym(i, j)] = fma(-u0[i], u0[j], fma(-u1[i], u1[j], c[sym(i, j)]));
+    }
+}
+
+// DEFER: the covariance part is left to the caller (downdate6 with u0, u1).
+template <bool COMPENSATED, unsigned SKIP = 0, bool DEFER = false, class T>
 __device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], const T (&b)[6],
-                                       T S00, T S01, T S11, T r0, T r1) {
+                                       T S00, T S01, T S11, T r0, T r1, T (&u0)[6], T (&u1)[6]) {
   const Sqrt2<COMPENSATED, T> q(S00, S01, S11);
   T z0, z1;
   const T chi2 = q.chi2(r0, r1, z0, z1);
-  T u0[6], u1[6];
   // uncompensated: u1 = b (S00 w1) - a (S01 w1)
   const T al = q.S00 * q.w1, be = q.S01 * q.w1;
 #pragma unroll
@@ -1057,14 +1070,14 @@ __device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], c
     u1[i] = COMPENSATED ? q.cross(b[i], a[i]) * q.w1 : fma(b[i], al, -(a[i] * be));
     p[i] = fma(u0[i], z0, fma(u1[i], z1, p[i]));
   }
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      if ((SKIP & (1u << i)) || (SKIP & (1u << j))) continue;
-      c[sym(i, j)] = fma(-u0[i], u0[j], fma(-u1[i], u1[j], c[sym(i, j)]));
-    }
+  if constexpr (!DEFER) downdate6<SKIP>(c, u0, u1);
   return chi2;
+}
+template <bool COMPENSATED, unsigned SKIP = 0, class T>
+__device__ __forceinline__ T kalman_2d(T (&p)[6], T (&c)[21], const T (&a)[6], const T (&b)[6],
+                                       T S00, T S01, T S11, T r0, T r1) {
+  T u0[6], u1[6];
+  return kalman_2d<COMPENSATED, SKIP, false>(p, c, a, b, S00, S01, S11, r0, r1, u0, u1);
 }
 
 // c -= u0 u0^T + u1 u1^T on the local form.
@@ -1142,6 +1155,20 @@ __device__ __forceinline__ T update_z(T (&p)[6], T (&c)[21], const T (&m)[3], co
   }
   return kalman_2d<true, ZFREE ? (1u << 2) : 0u>(p, c, a, b, a[0] + v[0], b[0] + v[1],
                                                  b[1] + v[2], m[0] - p[0], m[1] - p[1]);
+}
+// update_z<true> with the covariance part deferred to the caller
+// (downdate6<1 << 2> with u0, u1).
+template <class T>
+__device__ __forceinline__ T update_z_deferred(T (&p)[6], T (&c)[21], const T (&m)[3],
+                                               const T (&v)[6], T (&u0)[6], T (&u1)[6]) {
+  T a[6], b[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    a[i] = c[sym(i, 0)];
+    b[i] = c[sym(i, 1)];
+  }
+  return kalman_2d<true, (1u << 2), true>(p, c, a, b, a[0] + v[0], b[0] + v[1], b[1] + v[2],
+                                          m[0] - p[0], m[1] - p[1], u0, u1);
 }
 
 // p2r update: H measures the position along the cylinder's azimuthal
