@@ -216,6 +216,36 @@ def test_one_candidate_on_strongly_turning_tracks_is_the_fit():
                  chi2_abs=1e-10)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+def test_unreachable_first_surface_returns_the_inputs(dtype):
+    """The finder, like the fit, hands back the inputs unchanged for a track
+    that cannot reach its first surface (it carries a projection of the input
+    covariance); the other tracks match the fit with their own hits."""
+    n = 600
+    i = np.arange(n)
+    pt = np.where(i % 3 == 0, 0.02, np.linspace(0.75, 9.0, n))
+    ts = inputs.generate(inputs.MODE_R, n, seed=23, pt=pt)
+    cs = inputs.CandidateSet(ts.hpos[:, None], ts.hcov[:, None], np.zeros((ts.nlayer, ts.n), np.int32))
+    f = fit.Fitter(fit.Geometry(ts.B, ts.surf, tol=1e-12 if dtype == np.float64 else 1e-6), None)
+    try:
+        got, _ = _find(f, ts, cs, dtype, gate=1e30)
+    finally:
+        f.close()
+    r = oracle.fit_set(ts)
+    first = (r["status"] & 1) != 0
+    assert first.sum() == (i % 3 == 0).sum()
+    assert np.array_equal(got["status"][first], r["status"][first])
+    for k, v in (("par", ts.par0), ("cov", ts.cov0)):
+        assert np.array_equal(got[k][:, first], v[:, first].astype(dtype)), k
+    assert (got["chi2"][first] == 0).all() and (got["chosen"][:, first] == -1).all()
+    ok = ~first
+    tol = 1e-9 if dtype == np.float64 else 1e-4
+    parity.check({k: (v[..., ok] if isinstance(v, np.ndarray) else v) for k, v in got.items()},
+                 {k: v[..., ok] for k, v in r.items() if isinstance(v, np.ndarray)},
+                 f"finder, first surface out of reach ({np.dtype(dtype).name})", rtol=tol,
+                 **({"chi2_abs": 1e-10} if dtype == np.float64 else {}))
+
+
 def test_stopped_tracks_and_argument_errors():
     surf = inputs.surfaces(inputs.MODE_R)
     n = 64

@@ -367,6 +367,39 @@ def test_no_intersection_status_matches_oracle():
     parity.check(gpu_util.trim(g, 0, n), r, "all tracks")
 
 
+@pytest.mark.parametrize("mode", [inputs.MODE_R, inputs.MODE_Z], ids=["p2r", "p2z"])
+def test_unreachable_first_surface_returns_the_inputs(mode):
+    """A track that cannot reach its first surface has nothing applied: its
+    outputs are its inputs bit for bit (the layer loop carries a projection of
+    the input covariance, so the kernel reads the inputs back), its status and
+    chi2 say so, and the other track of its pair fits as the oracle does.
+    p2r: pT = 0.02 GeV (2 rho < 4 cm) on tracks 0, 1, 3 of every 6, so pairs
+    with one, the other or both lanes stopped; p2z: eta of either sign (the
+    planes of tracks moving to -z are behind them)."""
+    n = 1200
+    if mode == inputs.MODE_R:
+        i = np.arange(n)
+        pt = np.where(np.isin(i % 6, [0, 1, 3]), 0.02, np.linspace(0.75, 9.0, n))
+        ts = inputs.generate(inputs.MODE_R, n, seed=21, pt=pt)
+    else:  # |eta| in [1.5, 2.5] (the p2z workload's range), either sign, in random order
+        ts = inputs.generate(inputs.MODE_Z, 3 * n, seed=22, eta_range=(-2.5, 2.5))
+        eta = -np.log(np.tan(0.5 * ts.par0[5].astype(np.float64)))
+        ts = ts.subset(np.nonzero(np.abs(eta) >= 1.5)[0][:n])
+        n = ts.n
+    g = gpu_util.run([ts])
+    r = oracle.fit_set(ts)
+    first = (r["status"] & 1) != 0
+    assert 0.2 * n < first.sum() < 0.8 * n
+    assert np.array_equal(r["par"][:, first], ts.par0[:, first].astype(np.float64))
+    diff = np.nonzero(g["status"][:n] != r["status"])[0]
+    assert diff.size == 0, (diff[:10], g["status"][diff[:10]], r["status"][diff[:10]],
+                            ts.par0[:, diff[:10]])
+    for k, v in (("par", ts.par0), ("cov", ts.cov0)):
+        assert np.array_equal(g[k][:, :n][:, first].view(np.uint32), v[:, first].view(np.uint32)), k
+    assert (g["chi2"][:n][first] == 0).all() and np.array_equal(g["q"][:n][first], ts.q[first])
+    parity.check(gpu_util.trim(g, 0, n), r, "first surface out of reach")
+
+
 def test_empty_and_zero_tracks():
     f = fit.Fitter(fit.Geometry(3.8, inputs.surfaces(0)), None)
     empty = torch.empty((6, 4), device="cuda")
