@@ -184,14 +184,28 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
     }
     return r;
   };
+  // The hit rows are walked with two pointers, one row stride per load: the
+  // 64-bit index products of the indexed form cost p2r 6 % more instructions
+  // and 4 % of its time.
+  const float* hpl = hp + (int64_t)(3 * l0) * ldh;
+  const float* hcl = hc + (int64_t)(6 * l0) * ldh;
   for (int l = l0; l < a.nlayer; ++l) {
     T m[3], v[6];
+    if (L == 0) {
+      const float* q = hpl;
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      fitk::ld(m[k], L == 0 ? hp + (3 * l + k) * ldh : a.hpos + ix<L>(3 * l + k, t, ldh, 3 * a.nlayer));
+      for (int k = 0; k < 3; ++k, q += ldh) fitk::ld(m[k], q);
+      hpl = q;
+      q = hcl;
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
-      fitk::ld(v[k], L == 0 ? hc + (6 * l + k) * ldh : a.hcov + ix<L>(6 * l + k, t, ldh, 6 * a.nlayer));
+      for (int k = 0; k < 6; ++k, q += ldh) fitk::ld(v[k], q);
+      hcl = q;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fitk::ld(m[k], a.hpos + ix<L>(3 * l + k, t, ldh, 3 * a.nlayer));
+#pragma unroll
+      for (int k = 0; k < 6; ++k) fitk::ld(v[k], a.hcov + ix<L>(6 * l + k, t, ldh, 6 * a.nlayer));
+    }
     const float sf = geo.surf.s[l];
     const T dkdw = s.qf * T(-geo.kB);
     M fail, nc = fitk::lt(T(1.f), T(0.f));
