@@ -152,8 +152,6 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
                                           unsigned (&iters)[Lanes<T>::n],
                                           typename Lanes<T>::M& alive) {
   using M = typename Lanes<T>::M;
-  const float* hp = a.hpos + t;
-  const float* hc = a.hcov + t;
   const int64_t ldh = a.ld_hit;
   // lanes that hit max_iter or flipped charge on some layer; the status bits
   // (with non-finite for lanes no longer alive) are set once, on return
@@ -184,27 +182,24 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
     }
     return r;
   };
-  // The hit rows are walked with two pointers, one row stride per load: the
-  // 64-bit index products of the indexed form cost p2r 6 % more instructions
-  // and 4 % of its time.
-  const float* hpl = hp + (int64_t)(3 * l0) * ldh;
-  const float* hcl = hc + (int64_t)(6 * l0) * ldh;
+  // The hit rows are walked with two pointers, one row stride per load (ld
+  // in SoA, 32 in AoSoA, where a track's rows follow each other within its
+  // tile): the 64-bit index products of the indexed form cost p2r 6 % more
+  // instructions and 4 % of its time.
+  const int64_t rs = L == 0 ? ldh : 32;
+  const float* hpl = a.hpos + ix<L>(3 * l0, t, ldh, 3 * a.nlayer);
+  const float* hcl = a.hcov + ix<L>(6 * l0, t, ldh, 6 * a.nlayer);
   for (int l = l0; l < a.nlayer; ++l) {
     T m[3], v[6];
-    if (L == 0) {
+    {
       const float* q = hpl;
 #pragma unroll
-      for (int k = 0; k < 3; ++k, q += ldh) fitk::ld(m[k], q);
+      for (int k = 0; k < 3; ++k, q += rs) fitk::ld(m[k], q);
       hpl = q;
       q = hcl;
 #pragma unroll
-      for (int k = 0; k < 6; ++k, q += ldh) fitk::ld(v[k], q);
+      for (int k = 0; k < 6; ++k, q += rs) fitk::ld(v[k], q);
       hcl = q;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) fitk::ld(m[k], a.hpos + ix<L>(3 * l + k, t, ldh, 3 * a.nlayer));
-#pragma unroll
-      for (int k = 0; k < 6; ++k) fitk::ld(v[k], a.hcov + ix<L>(6 * l + k, t, ldh, 6 * a.nlayer));
     }
     const float sf = geo.surf.s[l];
     const T dkdw = s.qf * T(-geo.kB);
