@@ -108,12 +108,23 @@ __global__ void __launch_bounds__(kBlock) fit_find_kernel(const __grid_constant_
       const T* cc = a.ccov + (int64_t)l * a.ncand * 6 * ldc + t;
       int best = -1;
       T best_chi2 = a.gate;
+      // p2z walks the candidate rows with pointers (13 % faster there); the
+      // p2r loop measured 60 % slower that way and keeps the indexed form
+      const T* qp = cp;
+      const T* qc = cc;
       for (int k = 0; k < a.ncand; ++k) {
         T m[3], v[6];
+        if constexpr (MODE == FIT_MODE_Z) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j) fitk::ld(m[j], cp + (3 * k + j) * ldc);
+          for (int j = 0; j < 3; ++j, qp += ldc) fitk::ld(m[j], qp);
 #pragma unroll
-        for (int j = 0; j < 6; ++j) fitk::ld(v[j], cc + (6 * k + j) * ldc);
+          for (int j = 0; j < 6; ++j, qc += ldc) fitk::ld(v[j], qc);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 3; ++j) fitk::ld(m[j], cp + (3 * k + j) * ldc);
+#pragma unroll
+          for (int j = 0; j < 6; ++j) fitk::ld(v[j], cc + (6 * k + j) * ldc);
+        }
         const T x = (MODE == FIT_MODE_Z) ? fitk::chi2_z(p, c, m, v)
                                          : fitk::chi2_r_local(p, cl, bc, bs, m, v);
         if (x < best_chi2) {
