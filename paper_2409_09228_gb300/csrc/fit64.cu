@@ -39,12 +39,14 @@ struct Args64 {
 };
 
 // One track per thread over all layers; status bits, per-layer chi2 and
-// counters as fit_fused_kernel.
+// counters as fit_fused_kernel, and the covariance in the same loop form
+// (fused.cuh, enter_loop_form): p2z with its zero z row, p2r in the
+// cylinder's local coordinates.
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) fit_f64_kernel(const __grid_constant__ Args64 a) {
   const int64_t t = a.t0 + (int64_t)blockIdx.x * kBlock + threadIdx.x;
   if (t >= a.t1) return;
-  double p[6], c[21];
+  double p[6], c[21], cl[15], bc = 0.0, bs = 0.0;
 #pragma unroll
   for (int k = 0; k < 6; ++k) fitk::ld(p[k], a.par_in + k * a.ld_in + t);
 #pragma unroll
@@ -52,6 +54,17 @@ __global__ void __launch_bounds__(kBlock) fit_f64_kernel(const __grid_constant__
   double qf = (double)__ldcs(a.q_in + t);
   double chi2 = 0.0;
   fitk::Trig<double> g = fitk::trig_of(p);
+  {
+    const double kappa = qf * -a.kB * p[3];
+    if (MODE == FIT_MODE_Z) {
+      fitk::enter_plane(c, g, kappa);
+    } else {
+      fitk::enter_line(c, g, kappa, cl);
+      bc = g.cphi;
+      bs = g.sphi;
+    }
+  }
+  bool moved = false;  // some propagation was applied
   unsigned st = 0u, iters[1] = {0u};
   const Geo& geo = a.geo;
   const int64_t ldh = a.ld_hit;
@@ -64,20 +77,29 @@ __global__ void __launch_bounds__(kBlock) fit_f64_kernel(const __grid_constant__
     const float sf = geo.surf.s[l];
     const double dkdw = qf * -a.kB;
     bool nc = false, failed;
+    double lag = 0.0;
     if (MODE == FIT_MODE_Z)
-      failed = fitk::prop_z(p, c, g, dkdw, sf);
+      failed = fitk::prop_z<true>(p, c, g, dkdw, sf);
     else
-      failed = fitk::prop_r(p, c, g, dkdw, sf, geo.max_iter, geo.tol * sf,
-                            geo.line_start, iters, nc);
+      failed = fitk::prop_r_local(p, cl, bc, bs, g, dkdw, sf, geo.max_iter, geo.tol * sf,
+                                  geo.line_start, iters, nc, lag);
     if (failed) {
       st |= FIT_ST_NO_INTERSECTION;
       if (a.chi2_layer)
         for (int r = l; r < a.nlayer; ++r) a.chi2_layer[(int64_t)r * a.ld_out + t] = 0.0;
       break;
     }
+    moved = true;
     const double phi_pred = p[4], th_pred = p[5];
-    double x2 = (MODE == FIT_MODE_Z) ? fitk::update_z(p, c, m, v) : fitk::update_r(p, c, m, v);
-    const bool flip = fitk::normalise(p, c, qf, g, phi_pred, th_pred);
+    double x2;
+    bool flip;
+    if (MODE == FIT_MODE_Z) {
+      x2 = fitk::update_z<true>(p, c, m, v);
+      flip = fitk::normalise(p, c, qf, g, phi_pred, th_pred);
+    } else {
+      x2 = fitk::update_r_local(p, cl, bc, bs, m, v);
+      flip = fitk::normalise(p, cl, qf, g, phi_pred, th_pred, lag);
+    }
     const bool alive = fitk::finite_(x2);
     if (nc) st |= FIT_ST_NOT_CONVERGED;
     if (flip) st |= FIT_ST_CHARGE_FLIP;
@@ -90,6 +112,12 @@ __global__ void __launch_bounds__(kBlock) fit_f64_kernel(const __grid_constant__
         for (int r = l + 1; r < a.nlayer; ++r) a.chi2_layer[(int64_t)r * a.ld_out + t] = 0.0;
       break;
     }
+  }
+  if (!moved) {  // nothing applied: the input covariance
+#pragma unroll
+    for (int k = 0; k < 21; ++k) fitk::ld(c[k], a.cov_in + k * a.ld_in + t);
+  } else if (MODE == FIT_MODE_R) {
+    fitk::to_global_r(cl, bc, bs, c);
   }
   bool fin = isfinite(chi2);
 #pragma unroll
