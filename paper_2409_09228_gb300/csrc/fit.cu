@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kBlock, MODE == FIT_MODE_Z ? 4 : 3)
   const int64_t t = pair_track(a);
   if (t >= a.t1) return;
   unsigned st[2] = {0u, 0u}, iters[2] = {0u, 0u};
-  run_pair<MODE, L>(a, a.geo, a.t0, a.t1, t, st, iters);
+  run_pair<MODE, L, MODE == FIT_MODE_Z && L == 0>(a, a.geo, a.t0, a.t1, t, st, iters);
   if (st[0]) count_status(st[0], a.counters);
   if (st[1]) count_status(st[1], a.counters);
   if (MODE == FIT_MODE_R) count_iterations(iters[0] + iters[1], &a.counters[4]);

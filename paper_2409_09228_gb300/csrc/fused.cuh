@@ -15,6 +15,20 @@
 
 namespace fitimpl {
 
+// 8-byte asynchronous copy global -> shared (cp.async, completion per thread
+// through commit and wait groups).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void count_status(unsigned st, unsigned long long* counters) {
   if (st & FIT_ST_NO_INTERSECTION) atomicAdd(&counters[0], 1ull);
   if (st & FIT_ST_NOT_CONVERGED) atomicAdd(&counters[1], 1ull);
@@ -145,7 +159,13 @@ __device__ __forceinline__ void store_state(const FitArgs& a, int64_t t, const S
 // layer after one where a packed lane turned non-finite, or nlayer.  A lane
 // whose update turns non-finite stops (alive false); its later per-layer
 // chi2 entries are 0.
-template <int MODE, class T, int L = 0>
+//
+// STAGE (p2z, two tracks per thread, SoA, kBlock threads per block): the five
+// hit values the p2z update reads are copied one layer ahead into shared
+// memory with per-thread asynchronous copies, so that the short plane
+// propagation does not wait on their DRAM latency; each thread reads back
+// only what it copied itself, so no barrier is needed.
+template <int MODE, class T, int L = 0, bool STAGE = false>
 __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int64_t t, int l0,
                                           State<T>& s,
                                           unsigned (&st)[Lanes<T>::n],
@@ -173,6 +193,7 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
     for (int k = 0; k < NU; ++k) pu0[k] = pu1[k] = T(0.f);
   };
   auto done = [&](int r) {
+    if constexpr (STAGE) cp_async_wait<0>();
     settle();
 #pragma unroll
     for (int i = 0; i < Lanes<T>::n; ++i) {
@@ -189,9 +210,43 @@ __device__ __forceinline__ int run_layers(const FitArgs& a, const Geo& geo, int6
   const int64_t rs = L == 0 ? ldh : 32;
   const float* hpl = a.hpos + ix<L>(3 * l0, t, ldh, 3 * a.nlayer);
   const float* hcl = a.hcov + ix<L>(6 * l0, t, ldh, 6 * a.nlayer);
+  // STAGE: [layer parity][x, y, cov xx, yx, yy][thread]
+  static_assert(!STAGE || (MODE == FIT_MODE_Z && L == 0 && Lanes<T>::n == 2), "p2z pairs only");
+  __shared__ float2 hstage[STAGE ? 2 : 1][5][STAGE ? kBlock : 1];
+  auto stage = [&](int l) {
+    const float* p0 = a.hpos + ix<L>(3 * l, t, ldh, 3 * a.nlayer);
+    const float* c0 = a.hcov + ix<L>(6 * l, t, ldh, 6 * a.nlayer);
+    const int b = l & 1, x = threadIdx.x;
+    cp_async8(&hstage[b][0][x], p0);
+    cp_async8(&hstage[b][1][x], p0 + ldh);
+    cp_async8(&hstage[b][2][x], c0);
+    cp_async8(&hstage[b][3][x], c0 + ldh);
+    cp_async8(&hstage[b][4][x], c0 + 2 * ldh);
+    cp_async_commit();
+  };
+  if constexpr (STAGE) {
+    if (l0 < a.nlayer) stage(l0);
+  }
+  // (the layer l + 1 copy is issued before layer l's wait, so one copy is
+  // always in flight behind the layer being fitted)
   for (int l = l0; l < a.nlayer; ++l) {
     T m[3], v[6];
-    {
+    if constexpr (STAGE) {
+      if (l + 1 < a.nlayer) {
+        stage(l + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      const int b = l & 1, x = threadIdx.x;
+      m[0] = T(hstage[b][0][x]);
+      m[1] = T(hstage[b][1][x]);
+      m[2] = T(0.f);
+      v[0] = T(hstage[b][2][x]);
+      v[1] = T(hstage[b][3][x]);
+      v[2] = T(hstage[b][4][x]);
+      v[3] = v[4] = v[5] = T(0.f);
+    } else {
       const float* q = hpl;
 #pragma unroll
       for (int k = 0; k < 3; ++k, q += rs) fitk::ld(m[k], q);
@@ -301,7 +356,7 @@ __device__ __forceinline__ void finish_one(const FitArgs& a, const Geo& geo, int
 // (or, for p2r, whose crossing needs the one-lane form of the closed-form
 // start), from where each finishes alone.  One valid (the range starts or ends at an
 // odd index): that one alone.
-template <int MODE, int L = 0>
+template <int MODE, int L = 0, bool STAGE = false>
 __device__ __forceinline__ void run_pair(const FitArgs& a, const Geo& geo, int64_t t0, int64_t t1,
                                          int64_t t, unsigned (&st)[2], unsigned (&iters)[2]) {
   const bool v0 = t >= t0, v1 = t + 1 < t1;
@@ -309,7 +364,7 @@ __device__ __forceinline__ void run_pair(const FitArgs& a, const Geo& geo, int64
     State<F2> s;
     begin_state<MODE, L>(a, geo, t, s);
     fitk::M2 alive = {true, true};
-    const int l = run_layers<MODE, F2, L>(a, geo, t, 0, s, st, iters, alive);
+    const int l = run_layers<MODE, F2, L, STAGE>(a, geo, t, 0, s, st, iters, alive);
     if (l == a.nlayer) {
       finish_state<MODE, L>(a, t, l, s);
       store_state<L>(a, t, s, st);
