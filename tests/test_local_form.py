@@ -170,3 +170,17 @@ def test_start_projection_leaves_the_first_transport_unchanged(mode):
             assert np.abs(C0 @ np.array([cp, sp, 0, 0, 0, 0])).max() < 1e-15 * np.abs(C0).max() * 10
         err = np.abs(J @ C0 @ J.T - ref).max() / np.abs(ref).max()
         assert err < 1e-13, err
+
+
+def test_first_order_step_root_near_the_circle():
+    """The p2r step takes the first-order root -c2 / (2 b) of
+    d^2 + 2 b d + c2 = 0 when |c2| <= 1e-4 b^2: within 2.5e-5 of the exact
+    nearer root, which is itself below 5e-5 |b| (reading R4)."""
+    rng = np.random.default_rng(14)
+    b = rng.uniform(0.1, 120.0, 20000) * rng.choice([-1, 1], 20000)
+    c2 = rng.uniform(-1e-4, 1e-4, 20000) * b * b
+    exact = -c2 / (b + np.copysign(np.sqrt(b * b - c2), b))
+    first = -0.5 * c2 / b
+    rel = np.abs(first - exact) / np.maximum(np.abs(exact), 1e-300)
+    assert rel.max() <= 2.51e-5
+    assert (np.abs(exact) <= 5.0001e-5 * np.abs(b)).all()
