@@ -186,13 +186,12 @@ int fit_sync(fit_handle* h, void* stream, double timeout_s, fit_status* st);
  *                 and for such a copy the CUDA driver may wait for the work
  *                 queued earlier on `stream` before the call returns.
  * The work runs on the current CUDA device.  The first call on a device looks
- * up the device address of the fixed array (once per device); make that first
- * call before any stream capture begins.  That first call may also be where
- * CUDA loads the library's kernels onto the device (with lazy module loading,
- * CUDA's default), which allocates device memory for their code and for the
- * fixed array: make the first call while the process may still allocate (at
- * start-up), or set CUDA_MODULE_LOADING=EAGER so that loading happens when the
- * library is loaded.  Later calls allocate nothing.  Every call shares the one
+ * up the device address of the fixed array (once per device).  That first
+ * call may also be where CUDA loads the library's kernels onto the device
+ * (with lazy module loading, CUDA's default), which allocates device memory
+ * for their code and for the fixed array: make the first call while the
+ * process may still allocate (at start-up), or set CUDA_MODULE_LOADING=EAGER
+ * so that loading happens when the library is loaded.  Later calls allocate nothing.  Every call shares the one
  * array and each call clears the counters of its own events before its
  * kernels run, so calls whose work overlaps on the GPU (other streams, other
  * host threads) race on it: serialise them.
