@@ -29,8 +29,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 namespace {
 
-// 3 resident blocks per SM for p2r (152 registers, no spills; 2 blocks were
-// 17 % slower); p2z fits 4 (124 registers, no spills).
+// 3 resident blocks per SM for p2r (156 registers, no spills; 2 blocks were
+// 17 % slower); p2z fits 4 (128 registers, no spills).
 template <int MODE, int L = 0>
 __global__ void __launch_bounds__(kBlock, MODE == FIT_MODE_Z ? 4 : 3)
     fit_fused_kernel(const __grid_constant__ FitArgs a) {
