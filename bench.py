@@ -535,15 +535,15 @@ def bench_f64(args, world, rank, local):
             if record:
                 ev[m][1].record(stream)
 
+    clocks = ClockSampler(local)  # started before the warm-up, as in the headline
+    clocks.start()
+    time.sleep(0.3)
     for _ in range(args.warmup):
         step()
     st = f.sync(stream)
     assert st["nonfinite"] == 0 and st["no_intersection"] == 0, st
     torch.cuda.synchronize(dev)
     barrier(world)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
@@ -806,14 +806,14 @@ def bench_seed(args, world, rank, local):
     for label, fitter, net in (("straight_line", f, None), ("network", f, m),
                                ("crossing", fc, None)):
         fit.fit_mlp_attach(fitter.h, net, stream=stream)
+        if net is not None:  # started before the warm-up, as in the headline
+            clocks = ClockSampler(local)
+            clocks.start()
+            time.sleep(0.3)
         for _ in range(args.warmup):
             fitter.run(*d, [n], [0], out=out, stream=stream)
         fitter.sync(stream)
         barrier(world)
-        if net is not None:
-            clocks = ClockSampler(local)
-            clocks.start()
-            time.sleep(0.3)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
@@ -987,6 +987,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the other workloads after the headline measurement")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--one-stream", action="store_true",
+                    help="time the step with both modes on one stream (default: two streams)")
     ap.add_argument("--nevt", type=int, default=NEVT, help="events per mode (default 100)")
     ap.add_argument("--workload", default="uniform",
                     choices=["uniform", "uneven", "adjoint", "seed", "f64", "layout", "find",
@@ -1028,8 +1030,12 @@ def main():
     outs = [f.outputs(n, ld=ld) for _ in sets]
     ntrk = [NTRK] * NEVT
     stream = torch.cuda.current_stream(dev)
+    side = torch.cuda.Stream(dev)
+    fork, join = torch.cuda.Event(), torch.cuda.Event()
 
     def step(events=None):
+        # both modes on one stream, one after the other (each launch
+        # bracketed by events: the per-kernel times of the roofline)
         for m in (0, 1):
             if events is not None:
                 events[m][0].record(stream)
@@ -1037,28 +1043,54 @@ def main():
             if events is not None:
                 events[m][1].record(stream)
 
+    def step_two_streams():
+        # The p2r and p2z events are independent: p2z runs on a second stream,
+        # so that its blocks take the SMs that p2r's last wave leaves idle;
+        # the step ends when both have.
+        fork.record(stream)
+        side.wait_event(fork)
+        f.run(*dev_in[0], ntrk, [0] * NEVT, out=outs[0], stream=stream)
+        f.run(*dev_in[1], ntrk, [1] * NEVT, out=outs[1], stream=side)
+        join.record(side)
+        stream.wait_event(join)
+
     fp32_probe = measure_fp32(local)
-    for _ in range(args.warmup):
-        step()
-    st = f.sync(stream)
-    assert st["nonfinite"] == 0 and st["no_intersection"] == 0, st
     per = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(2)]
            for _ in range(args.steps)]
     t_begin, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    barrier(world)
+    # The clock record starts before the warm-up steps, so that the GPU comes
+    # to the timed region from them (through one synchronize), not from an
+    # idle pause, which cost the first timed steps ~3 %.
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    for _ in range(args.warmup):
+        step() if args.one_stream else step_two_streams()
+    st = f.sync(stream)
+    assert st["nonfinite"] == 0 and st["no_intersection"] == 0, st
+    torch.cuda.synchronize(dev)
+    barrier(world)
     t_begin.record(stream)
     for k in range(args.steps):
-        step(per[k])
+        step(per[k]) if args.one_stream else step_two_streams()
     t_end.record(stream)
     torch.cuda.synchronize(dev)
+    ms = t_begin.elapsed_time(t_end) / args.steps
+    ms_one_stream = ms
+    if not args.one_stream:
+        # the per-kernel times, each kernel alone on the GPU: as many steps
+        # again on one stream, inside the clock record
+        s_begin, s_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_begin.record(stream)
+        for k in range(args.steps):
+            step(per[k])
+        s_end.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_one_stream = s_begin.elapsed_time(s_end) / args.steps
     clk = clocks.stop()
     barrier(world)
-    ms = t_begin.elapsed_time(t_end) / args.steps
     ms = max_over_ranks(world, ms)
+    ms_one_stream = max_over_ranks(world, ms_one_stream)
     kernel_ms = [statistics.mean(per[k][m][0].elapsed_time(per[k][m][1]) for k in range(args.steps))
                  for m in (0, 1)]
     st = f.sync(stream)
@@ -1066,7 +1098,9 @@ def main():
     value = world * units_per_step / (ms / 1e3)
 
     # iterations of the p2r path-length step per track-layer, counted by the kernel
-    it_per = st["iterations"] / max(1, args.steps * n * NLAYER)
+    # (the counters hold both timed passes with two streams)
+    passes = 1 if args.one_stream else 2
+    it_per = st["iterations"] / max(1, passes * args.steps * n * NLAYER)
     flops = [flops_p2r(it_per), FLOPS_P2Z]
     mufu = [mufu_p2r(it_per), MUFU_P2Z]
     dom = int(np.argmax(kernel_ms))
@@ -1183,7 +1217,9 @@ def main():
                                         "fused kernels read the page-locked inputs and write the "
                                         "outputs over the host link, no staging copies"},
                     "ms_per_step": e2e_ms},
-            "gpu_launches": 2 * args.steps, "p2r_iterations_per_track_layer": it_per,
+            "gpu_launches": 2 * args.steps,
+            "step_streams": 1 if args.one_stream else 2, "ms_per_step_one_stream": ms_one_stream,
+            "p2r_iterations_per_track_layer": it_per,
             "p2r_straight_line_start": line_start}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sets)
