@@ -1060,7 +1060,7 @@ def main():
     t_begin, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # The clock record starts before the warm-up steps, so that the GPU comes
     # to the timed region from them (through one synchronize), not from an
-    # idle pause, which cost the first timed steps ~3 %.
+    # idle pause, which cost the timed steps ~2 %.
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -1075,6 +1075,7 @@ def main():
         step(per[k]) if args.one_stream else step_two_streams()
     t_end.record(stream)
     torch.cuda.synchronize(dev)
+    barrier(world)
     ms = t_begin.elapsed_time(t_end) / args.steps
     ms_one_stream = ms
     if not args.one_stream:
