@@ -290,38 +290,6 @@ constexpr unsigned long long kER =
     bit(2, 0) | bit(2, 1) | bit(2, 3) | bit(2, 4) | bit(2, 5) |
     bit(4, 0) | bit(4, 1) | bit(4, 3) | bit(4, 4);
 
-// c <- J c J^T on the packed lower triangle.  With J = diag + E every product
-// chain starts from the entry it corrects (JC_ij = c_ij + sum_k E_ik c_kj,
-// C'_ij = JC_ij + sum_k JC_ik E_jk), so no chain needs a separate multiply.
-// With the loops unrolled the mask tests fold at compile time.
-template <unsigned ROWS, unsigned long long EMASK, class T>
-__device__ __forceinline__ void similarity(const T (&E)[6][6], T (&c)[21]) {
-  T JC[6][6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      T acc = (ROWS & row(i)) ? c[sym(i, j)] : T(0.f);
-#pragma unroll
-      for (int k = 0; k < 6; ++k)
-        if (EMASK & bit(i, k)) acc = fma(E[i][k], c[sym(k, j)], acc);
-      JC[i][j] = acc;
-    }
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      T acc = T(0.f);
-      if ((ROWS & row(i)) && (ROWS & row(j))) {  // a vanishing row gives 0
-        acc = JC[i][j];
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-          if (EMASK & bit(j, k)) acc = fma(JC[i][k], E[j][k], acc);
-      }
-      c[sym(i, j)] = acc;
-    }
-}
-
 // c <- J c J^T through the structure of the propagate-to-surface Jacobian,
 // J = A + v g^T: A = I + E_h is the derivative of the helix at a fixed path
 // length h, v = d p' / d h, and g = grad h, the dependence of h on the
@@ -1243,34 +1211,16 @@ __device__ __forceinline__ T chi2_r_local(const T (&p)[6], const T (&cl)[15], T 
   return Sqrt2<false, T>(h.S00, h.S01, h.S11).chi2(h.r0, h.r1, z0, z1);
 }
 
-// chi2 = r^T S^-1 r of a hit against the prediction, without the update
-// (track finding tries every candidate).  The same expressions as
-// update_z / update_r and kalman_2d, so the chi2 of the chosen candidate is
-// the one its update returns.
+// chi2 = r^T S^-1 r of a hit on a plane against the prediction, without the
+// update (track finding tries every candidate; chi2_r_local on a cylinder).
+// The same expressions as update_z and kalman_2d, so the chi2 of the chosen
+// candidate is the one its update returns.
 template <class T>
 __device__ __forceinline__ T chi2_z(const T (&p)[6], const T (&c)[21], const T (&m)[3],
                                     const T (&v)[6]) {
   const T S00 = c[sym(0, 0)] + v[0], S01 = c[sym(1, 0)] + v[1], S11 = c[sym(1, 1)] + v[2];
   T z0, z1;
   return Sqrt2<true, T>(S00, S01, S11).chi2(m[0] - p[0], m[1] - p[1], z0, z1);
-}
-template <class T>
-__device__ __forceinline__ T chi2_r(const T (&p)[6], const T (&c)[21], const T (&m)[3],
-                                    const T (&v)[6]) {
-  const T ir = frsqrt(fma(m[0], m[0], m[1] * m[1]));
-  const T sh = m[1] * ir, ch = m[0] * ir;
-  const T a0 = fma(ch, c[sym(0, 1)], -(sh * c[sym(0, 0)]));
-  const T a1 = fma(ch, c[sym(1, 1)], -(sh * c[sym(1, 0)]));
-  const T a2 = fma(ch, c[sym(2, 1)], -(sh * c[sym(2, 0)]));
-  const T vtt = fma(sh * sh, v[0], fma(ch * ch, v[2], T(-2.f) * sh * ch * v[1]));
-  const T vtz = fma(ch, v[4], -(sh * v[3]));
-  const T S00 = fma(ch, a1, -(sh * a0)) + vtt;
-  const T S01 = a2 + vtz;
-  const T S11 = c[sym(2, 2)] + v[5];
-  const T r0 = fma(ch, m[1] - p[1], -(sh * (m[0] - p[0])));
-  const T r1 = m[2] - p[2];
-  T z0, z1;
-  return Sqrt2<false, T>(S00, S01, S11).chi2(r0, r1, z0, z1);
 }
 
 }  // namespace fitk
