@@ -128,7 +128,8 @@ typedef struct {
  * fit_init: creates a handle on CUDA device `device` for the two modes.
  * cfg_r / cfg_z describe the p2r cylinders and the p2z planes; either may be
  * NULL if that mode is never used.  The handle allocates its own small device
- * scratch (status counters) and frees it in fit_destroy.
+ * scratch (status counters) and creates a second CUDA stream with two events
+ * (see fit_propagate_update); fit_destroy frees them.
  * Errors: FIT_ERR_ARG (bad config), FIT_ERR_CUDA, FIT_ERR_NOMEM.
  */
 int fit_init(fit_handle** h, const fit_config* cfg_r, const fit_config* cfg_z, int device);
@@ -141,7 +142,11 @@ int fit_init(fit_handle** h, const fit_config* cfg_r, const fit_config* cfg_z, i
  * update with hit l.  Track t of the concatenation reads in.par[k*in.ld + t],
  * hits.pos[(l*3 + k)*hits.ld + t], ... and writes out.par[k*out.ld + t], ...
  * nlayer must equal the configured nlayer of every mode used.
- * Consecutive events of the same mode run as one kernel launch.
+ * Consecutive events of the same mode run as one kernel launch.  A call with
+ * events of both modes runs its p2z launches on the handle's second stream,
+ * forked from `stream` before them and joined back after them, so that they
+ * overlap the p2r launches; `stream` follows the whole call as before.  Calls
+ * on one handle from several host threads take turns for that stream.
  * Errors: FIT_ERR_ARG (NULL pointer, misaligned pointer or ld, sizes out of
  * range, unconfigured mode), FIT_ERR_CUDA (launch failure).
  */

@@ -175,13 +175,13 @@ int launch_segments(const fit_handle* h, FitArgs a, int nevt, const int64_t* ntr
 }
 
 // The fused fit of events [0, nevt) on the tracks of a (a.t0, a.t1 set per
-// run of same-mode events), on stream s.
+// run of same-mode events): the p2r runs on stream s, the p2z runs on sz.
 int run_fit(const fit_handle* h, const FitArgs& a, int nevt, const int64_t* ntrk,
-            const int32_t* mode, const char* who, cudaStream_t s) {
+            const int32_t* mode, const char* who, cudaStream_t s, cudaStream_t sz) {
   return launch_segments(h, a, nevt, ntrk, mode, who,
-                         [s, h](const FitArgs& a1, int m, unsigned nblk, int, int) {
+                         [s, sz, h](const FitArgs& a1, int m, unsigned nblk, int, int) {
                            if (m == FIT_MODE_Z)
-                             fit_fused_kernel<FIT_MODE_Z><<<nblk, kBlock, 0, s>>>(a1);
+                             fit_fused_kernel<FIT_MODE_Z><<<nblk, kBlock, 0, sz>>>(a1);
                            else if (h->seeded)
                              launch_seeded_fit(a1, h->d_mlp, s);
                            else
@@ -249,10 +249,16 @@ int fit_init(fit_handle** out, const fit_config* cfg_r, const fit_config* cfg_z,
     return fail(FIT_ERR_NOMEM, std::string("fit_init: cudaMalloc: ") + cudaGetErrorString(e));
   }
   e = cudaMemset(h->d_counters, 0, kCounters * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
+    if (h->join) cudaEventDestroy(h->join);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->side) cudaStreamDestroy(h->side);
     cudaFree(h->d_counters);
     delete h;
-    return cuda_fail(e, "fit_init: cudaMemset");
+    return cuda_fail(e, "fit_init: counters, stream and events");
   }
   *out = h;
   return FIT_OK;
@@ -267,8 +273,30 @@ int fit_propagate_update(fit_handle* h, const fit_tracks_in* in, const fit_track
   int rc = check_call(h, in, out, hits, nevt, ntrk, nlayer, mode, &total, "fit_propagate_update");
   if (rc != FIT_OK || total == 0) return rc;
   DeviceGuard g(h->device);
-  rc = run_fit(h, base_args(in, out, hits, nlayer, h->d_counters), nevt, ntrk, mode,
-               "fit_propagate_update", static_cast<cudaStream_t>(stream));
+  static const char* kWho = "fit_propagate_update";
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const FitArgs a = base_args(in, out, hits, nlayer, h->d_counters);
+  bool used[2] = {false, false};
+  for (int e = 0; e < nevt; ++e)
+    if (ntrk[e] > 0) used[mode[e] == FIT_MODE_Z] = true;
+  if (!(used[0] && used[1])) {
+    rc = run_fit(h, a, nevt, ntrk, mode, kWho, s, s);
+  } else {
+    // The two modes' events are independent: the p2z launches go to the
+    // handle's second stream, so that they overlap the p2r launches (their
+    // blocks fill the SMs a launch's last wave leaves idle).  The join is
+    // recorded even after a failed launch, so that the caller's stream
+    // still follows everything that was queued.
+    std::lock_guard<std::mutex> lock(h->side_mu);
+    cudaError_t e = cudaEventRecord(h->fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "fit_propagate_update: fork to the second stream");
+    rc = run_fit(h, a, nevt, ntrk, mode, kWho, s, h->side);
+    e = cudaEventRecord(h->join, h->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->join, 0);
+    if (e != cudaSuccess && rc == FIT_OK)
+      return cuda_fail(e, "fit_propagate_update: join from the second stream");
+  }
   if (rc != FIT_OK) return rc;
   h->tracks += (uint64_t)total;
   return FIT_OK;
@@ -406,6 +434,9 @@ void fit_destroy(fit_handle* h) {
     if (h->d_counters || h->d_mlp || h->host_stage) cudaDeviceSynchronize();
     if (h->d_counters) cudaFree(h->d_counters);
     if (h->d_mlp) cudaFree(h->d_mlp);
+    if (h->join) cudaEventDestroy(h->join);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->side) cudaStreamDestroy(h->side);
     destroy_host_stage(h);
   }
   delete h;

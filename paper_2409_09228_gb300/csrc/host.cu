@@ -184,7 +184,7 @@ extern "C" int fit_propagate_update_host(fit_handle* h, const fit_tracks_in* in,
                         out->status ? S.status : nullptr, hs->cap};
     fit_hits shit{S.hpos, S.hcov, hs->cap};
     rc = run_fit(h, base_args(&sin, &sout, &shit, nlayer, h->d_counters), (int)nt_local.size(),
-                 nt_local.data(), md_local.data(), kWho, s);
+                 nt_local.data(), md_local.data(), kWho, s, s);
     if (rc != FIT_OK) return rc;
     e = copy_rows(out->par + c0, pout, S.par, P, w, 6, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = copy_rows(out->cov + c0, pout, S.cov, P, w, 21, cudaMemcpyDeviceToHost, s);
@@ -240,7 +240,7 @@ extern "C" int fit_propagate_update_mapped(fit_handle* h, const fit_tracks_in* i
                                    ": a buffer is not page-locked host memory mapped into the "
                                    "device's address space");
   rc = run_fit(h, base_args(in, out, hits, nlayer, h->d_counters), nevt, ntrk, mode, kWho,
-               static_cast<cudaStream_t>(stream));
+               static_cast<cudaStream_t>(stream), static_cast<cudaStream_t>(stream));
   if (rc != FIT_OK) return rc;
   h->tracks += (uint64_t)total;
   return FIT_OK;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "fit.h"
@@ -83,6 +84,12 @@ struct fit_handle {
   bool seeded = false;    // p2r seeds from d_mlp
   void* host_stage = nullptr;  // staging of fit_propagate_update_host (host.cu)
   float B[2] = {0.f, 0.f};     // field of each mode's configuration
+  // A call of fit_propagate_update with events of both modes runs its p2z
+  // launches on `side`, forked from the caller's stream by `fork` and joined
+  // back by `join`; side_mu keeps concurrent calls from interleaving them.
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  std::mutex side_mu;
 };
 
 
@@ -100,9 +107,9 @@ FitArgs base_args(const fit_tracks_in* in, const fit_tracks_out* out, const fit_
 void launch_seeded_fit(const FitArgs& a, const void* img, cudaStream_t s);
 
 // The fused fit of events [0, nevt) (fit.cu): one launch per run of
-// same-mode events, on stream s.
+// same-mode events, the p2r runs on stream s and the p2z runs on sz.
 int run_fit(const fit_handle* h, const FitArgs& a, int nevt, const int64_t* ntrk,
-            const int32_t* mode, const char* who, cudaStream_t s);
+            const int32_t* mode, const char* who, cudaStream_t s, cudaStream_t sz);
 
 // Frees the staging of fit_propagate_update_host (host.cu).
 void destroy_host_stage(fit_handle* h);

@@ -71,6 +71,43 @@ def test_multi_event_mixed_modes():
     assert g["sync"]["tracks"] == sum(sizes)
 
 
+def test_mixed_modes_are_joined_back_to_the_callers_stream():
+    """A call with events of both modes runs its p2z launches on the handle's
+    second stream and joins them back to the caller's.  With a large p2z
+    event between two small p2r events, synchronising the caller's stream
+    alone must find every output written (NaN and 0xff before the call) and
+    matching the oracle; the counters must hold every track."""
+    sets = [inputs.generate(inputs.MODE_R, 64, seed=301),
+            inputs.generate(inputs.MODE_Z, 200000, seed=302),
+            inputs.generate(inputs.MODE_R, 33, seed=303)]
+    f = fit.Fitter(fit.Geometry(sets[0].B, sets[0].surf), fit.Geometry(sets[1].B, sets[1].surf))
+    try:
+        c = gpu_util.concat(sets)
+        n = c["par0"].shape[-1]
+        ld = gpu_util.pad_ld(n)
+        d = [gpu_util.to_dev(c[k], ld) for k in ("par0", "cov0", "q", "hpos", "hcov")]
+        out = f.outputs(n, ld=ld)
+        for k in ("par", "cov", "chi2"):
+            out[k].fill_(float("nan"))
+        out["status"].fill_(0xff)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        f.run(*d, [x.n for x in sets], [x.mode for x in sets], out=out, stream=s)
+        s.synchronize()
+        got = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+        st = f.sync(s)
+    finally:
+        f.close()
+    assert (got["status"][:n] != 0xff).all()
+    fin = (got["status"][:n] & fit.FIT_ST_NONFINITE) == 0
+    assert np.isfinite(got["par"][:, :n][:, fin]).all() and np.isfinite(got["chi2"][:n][fin]).all()
+    assert st["tracks"] == n
+    t = 0
+    for x in sets:
+        parity.check(gpu_util.trim(got, t, t + x.n), oracle.fit_set(x), f"event at {t}")
+        t += x.n
+
+
 @pytest.mark.parametrize("start", [fit.FIT_START_CROSSING, fit.FIT_START_LINE],
                          ids=["crossing", "line"])
 def test_p2r_starts_reach_the_oracles_crossing(start):
